@@ -1,0 +1,75 @@
+"""Query plans of the evaluated workloads, as neutral plan dicts (data only).
+
+A plan is the pipeline program(s) of one query (Table 2): optional build
+pipelines (FILTER + HASH_PUT on a dimension), then one probe/scan pipeline
+(LOOP, FILTER, HASH_PROBE*, ARITHMETIC, then AGGREGATE, HASH_AGGREGATE or
+PROJECT).  The format is documented in the Python binding
+(``paper_1709_00700_gb300.pv.plan_to_spec``); it carries no arithmetic.
+"""
+from __future__ import annotations
+
+from . import datagen
+
+# Plain filter-aggregate / filter-project query on the 1M-row table:
+#   WHERE a < 10 AND 20 <= b <= 40  -> SUM(price), COUNT(*)  and  (a, price) rows.
+def filter_agg_plan(a_lt: int = 10, b_lo: int = 20, b_hi: int = 40) -> dict:
+    return {"fact": "t", "filters": [["a", "lt", a_lt], ["b", "between", b_lo, b_hi]],
+            "aggs": [["sum", [["x", "price"]]], ["count"]]}
+
+
+def filter_project_plan(a_lt: int = 10, b_lo: int = 20, b_hi: int = 40) -> dict:
+    return {"fact": "t", "filters": [["a", "lt", a_lt], ["b", "between", b_lo, b_hi]],
+            "project": ["a", "price"]}
+
+
+# Low-cardinality grouped aggregation (4 groups, 8 aggregates of fixed-point
+# products), shaped like the compute-heavy aggregation pipeline of TPC-H Q1.
+LOWCARD_DAY_HI = datagen.DAY0 + 2475
+
+
+def lowcard_plan(day_hi: int = LOWCARD_DAY_HI) -> dict:
+    return {
+        "fact": "li",
+        "filters": [["date", "le", day_hi]],
+        "group_by": ["k1", "k2"],
+        "aggs": [
+            ["sum", [["x", "qty"]]],
+            ["sum", [["x", "price"]]],
+            ["sum", [["x", "disc"]]],
+            ["sum", [["x", "tax"]]],
+            ["sum", [["x", "price"], ["c_minus_x", "disc", 100]]],
+            ["sum", [["x", "price"], ["c_minus_x", "disc", 100], ["x_plus_c", "tax", 100]]],
+            ["sum", [["x", "qty"], ["x", "price"]]],
+            ["count"],
+        ],
+    }
+
+
+# High-cardinality grouped aggregation: SUM(val), COUNT(*) GROUP BY key,
+# optionally filtered on val (selectivity knob of the random query suite).
+def keyval_plan(val_lt: int | None = None) -> dict:
+    p = {"fact": "kv", "group_by": ["key"], "aggs": [["sum", [["x", "val"]]], ["count"]]}
+    if val_lt is not None:
+        p["filters"] = [["val", "lt", val_lt]]
+    return p
+
+
+# Star join shaped like SSB Q4.1: four build pipelines (dimension filter
+# f < t, HASH_PUT key with the grouping attribute as payload) and one probe
+# pipeline that probes all four and groups on two dimension attributes.
+STAR_THRESHOLDS = {"d_a": 20, "d_b": 20, "d_c": 5, "d_d": 10}
+STAR_PROBE_ORDER = ("d_c", "d_d", "d_a", "d_b")   # most selective first
+
+
+def star_plan(thresholds: dict | None = None, order=STAR_PROBE_ORDER) -> dict:
+    th = dict(STAR_THRESHOLDS)
+    th.update(thresholds or {})
+    builds, probes = [], []
+    for name in order:
+        pay = ["g"] if name in ("d_a", "d_b") else []
+        builds.append({"table": name, "key": "key", "filters": [["f", "lt", th[name]]], "payload": pay})
+        probes.append({"build": len(builds) - 1, "fk": "fk_" + name[2:]})
+    ia, ib = order.index("d_a"), order.index("d_b")
+    return {"fact": "fact", "builds": builds, "probes": probes,
+            "group_by": [["payload", ia, 0], ["payload", ib, 0]],
+            "aggs": [["sum", [["x", "revenue"]]], ["count"]]}
