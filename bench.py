@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Throughput of the query-pipeline hot path on GB300.
+
+Default workload: low-cardinality grouped aggregation on a 6M-row synthetic
+fact table (int32 date over 2526 days filtered to ~98%, two one-byte group
+codes -> 4 groups, int64 fixed-point qty/price/discount/tax, 8 aggregates of
+fixed-point products).  One step = one whole pipeline run (scan, filter,
+arithmetic, HASH_AGGREGATE, result extraction) through the C ABI.
+
+Prints one JSON line: rows/s, the roofline of the dominant kernel (HBM),
+the CPU oracle timed on this host, an end-to-end figure with host buffers,
+and the SM clocks sampled during the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pv|reference]
+                    [--workload lowcard|filter_agg|filter_project|keyval|star]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1709_00700_gb300 import datagen, workloads  # noqa: E402
+
+METRIC = "rows/s & % of HBM peak per query; learned-pick time vs exhaustive-best variant"
+UNIT = "rows/s"
+
+# Algorithmic bytes per row: the bytes the query must read from the columns it
+# references (every row of every referenced column) plus what it writes.
+WORKLOADS = {
+    "lowcard": dict(rows=6_000_000, bytes_per_row=4 + 1 + 1 + 4 * 8,
+                    desc="low-cardinality grouped aggregation, 6M rows, 4 groups, 8 aggregates"),
+    "filter_agg": dict(rows=1_000_000, bytes_per_row=16,
+                       desc="filter a<10 AND 20<=b<=40 -> SUM(price), COUNT(*), 1M rows"),
+    "filter_project": dict(rows=1_000_000, bytes_per_row=16,
+                           desc="filter a<10 AND 20<=b<=40 -> (a, price) rows, 1M rows"),
+    "keyval": dict(rows=60_000_000, bytes_per_row=12,
+                   desc="SUM(val), COUNT(*) GROUP BY key, 60M rows, G groups"),
+    "star": dict(rows=60_000_000, bytes_per_row=24,
+                 desc="four-probe star join grouped on two dimension attributes, 60M fact rows"),
+}
+
+# Variant per workload (measured best so far; the autotuner refreshes these).
+TUNED = {
+    "lowcard": dict(agg="local", ht="perfect", threads_per_table=1, pred="branch", access="grid",
+                    items_per_thread=2, block=256),
+    "filter_agg": dict(pred="branch", access="grid", items_per_thread=2, block=256),
+    "filter_project": dict(exec="multi", pred="branch", access="grid", items_per_thread=4, block=256),
+    "keyval": dict(agg="global", ht="perfect", pred="branch", access="grid", items_per_thread=2, block=256),
+    "star": dict(agg="local", ht="perfect", pred="branch", access="grid", items_per_thread=2, block=256),
+}
+
+
+def make_tables(name: str, rows: int, groups: int):
+    if name == "lowcard":
+        return {"li": datagen.table_lowcard_groups(rows)}, workloads.lowcard_plan()
+    if name == "filter_agg":
+        return {"t": datagen.table_filter_agg(rows)}, workloads.filter_agg_plan()
+    if name == "filter_project":
+        return {"t": datagen.table_filter_agg(rows)}, workloads.filter_project_plan()
+    if name == "keyval":
+        return {"kv": datagen.table_keyval(rows, groups)}, workloads.keyval_plan()
+    if name == "star":
+        s = datagen.star_schema(rows)
+        return s, workloads.star_plan()
+    raise ValueError(name)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1709_00700_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    with open(os.path.join(ROOT, "include", "pv.h"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload: str):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, if it was taken on the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(workload)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    n = int(os.environ.get("WORLD_SIZE", "1"))
+    return int(os.environ.get("RANK", "0")), n, int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def init_dist(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        return dist
+    return None
+
+
+def max_over_ranks(dist, x: float) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def cpu_oracle_rate(plan, tables, budget_s: float, rows: int):
+    """The oracle as it stands, on all host cores, repeated for ~budget_s."""
+    from oracle import oracle
+    cores = oracle.hardware_threads()
+    oracle.run(plan, tables, nthreads=cores)  # build + warm
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        oracle.run(plan, tables, nthreads=cores)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or n >= 50:
+            break
+    return rows * n / el, cores, n
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = WORKLOADS[args.workload]
+    rows = args.rows or w["rows"]
+    tables, plan = make_tables(args.workload, rows, args.groups)
+    from oracle import oracle
+    cores = oracle.hardware_threads()
+    for _ in range(args.warmup):
+        oracle.run(plan, tables, nthreads=cores)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.run(plan, tables, nthreads=cores)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = rows * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic (seeded counter-based generator)",
+        "config": {"workload": w["desc"], "rows": rows, "seed": datagen.DEFAULT_SEED},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"the whole {rows}-row table per step, row-partitioned over {cores} threads"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_pv(args):
+    import torch
+
+    from paper_1709_00700_gb300 import pv
+    rank, world, local = dist_env()
+    dist = init_dist(world)
+    torch.cuda.set_device(local)
+    w = WORKLOADS[args.workload]
+    rows = args.rows or w["rows"]
+    tables, plan = make_tables(args.workload, rows, args.groups)
+    var_kw = dict(TUNED[args.workload])
+    if args.variant:
+        var_kw.update(json.loads(args.variant))
+    var = pv.variant(**var_kw)
+    ctx = pv.Context(local)
+    dev = {t: {c: torch.from_numpy(np.ascontiguousarray(v)).cuda(local) for c, v in cols.items()}
+           for t, cols in tables.items()}
+    for t, cols in dev.items():
+        ctx.register_table(t, cols)
+    hts = ctx.build_all(plan, pv.ht_variant(args.build_ht))
+    res = ctx.run(plan, var, hts)
+    ctx.sync()
+    first = [c.astype(np.int64) for c in ctx.fetch(res)]
+    nk = len(plan.get("group_by", []))
+    if args.workload == "lowcard":  # invariant at full size: the counts add up to the passing rows
+        passing = int((tables["li"]["date"] <= workloads.LOWCARD_DAY_HI).sum())
+        assert int(first[nk + 7].sum()) == passing, "count invariant failed"
+    stream = ctx.stream
+    ctx.set_kernel_timing(True)
+    for _ in range(args.warmup):
+        ctx.lib.pv_l2_flush(ctx.h)
+        ctx.rerun(res)
+    ctx.sync()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kernel_ms = []
+    launches_per_step = 0
+    barrier(dist)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            ctx.lib.pv_l2_flush(ctx.h)  # cold L2 before every step (outside the timed events)
+            starts[i].record(stream)
+            ctx.rerun(res)
+            ends[i].record(stream)
+            launches_per_step = ctx.last_launch_count()
+            kernel_ms.append(ctx.kernel_times())
+        torch.cuda.synchronize()
+    barrier(dist)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_s = max_over_ranks(dist, sum(step_ms) / 1000.0)
+    value = rows * world * args.steps / total_s
+    # dominant kernel: the longest one of the step
+    per_kernel = np.array([k for k in kernel_ms if k], dtype=np.float64)
+    dom = int(np.argmax(per_kernel.mean(axis=0)))
+    dom_ms = float(per_kernel[:, dom].mean())
+    peak, peak_kind = measured_peaks()
+    alg_bytes = w["bytes_per_row"] * rows
+    achieved = alg_bytes / (dom_ms / 1000.0) / 1e9
+    # end to end through the C ABI with host buffers: H2D of the step's input
+    # columns from pinned memory, the pipeline, D2H of the result
+    pinned = {t: {c: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for c, v in cols.items()}
+              for t, cols in tables.items()}
+    h2d = sum(v.numel() * v.element_size() for cols in pinned.values() for v in cols.values())
+    ctx.set_kernel_timing(False)
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(e2e_steps):
+        with torch.cuda.stream(stream):
+            for t, cols in pinned.items():
+                for c, v in cols.items():
+                    dev[t][c].copy_(v, non_blocking=True)
+        ctx.rerun(res)
+        out = ctx.fetch(res)
+        d2h = sum(a.nbytes for a in out) + 8
+    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(dist, e2e_s)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic (seeded counter-based generator)",
+        "config": {"workload": w["desc"], "rows": rows, "variant": var_kw,
+                   "l2": "flushed (2x L2 write) before every step, outside the timed events",
+                   "seed": datagen.DEFAULT_SEED, "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": ncu_traffic(args.workload),
+                     "kernel_index": dom, "kernel_ms": dom_ms, "algorithmic_bytes": alg_bytes,
+                     "peak_source": f"{peak_kind} hbm_gbs"},
+        "e2e": {"value": rows * world * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": (launches_per_step + 1) * args.steps,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, cores, n = cpu_oracle_rate(plan, tables, args.cpu_budget, rows)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"the whole {rows}-row table, {n} runs on {cores} threads"}
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="pv", choices=["pv", "reference"])
+    ap.add_argument("--workload", default="lowcard", choices=sorted(WORKLOADS))
+    ap.add_argument("--rows", type=int, default=0)
+    ap.add_argument("--groups", type=int, default=1000)
+    ap.add_argument("--variant", default="", help="JSON overrides of the pv_variant fields")
+    ap.add_argument("--build-ht", default="perfect")
+    ap.add_argument("--cpu-budget", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    return run_reference(args) if args.impl == "reference" else run_pv(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,257 @@
+/*
+ * libpv — query-pipeline code variants on one GB300 GPU (sm_103a).
+ *
+ * C ABI for the data-parallel hot path of Breß et al., "Generating Custom
+ * Code for Efficient Query Execution on Heterogeneous Processors":
+ *   register the columns of in-memory, column-major tables that already live
+ *   in device memory (Section 7.5: column store, data cached on the device
+ *   before execution, Section 9.1), build a hash table on a dimension in a
+ *   build pipeline (Table 2; HASH_PUT of Table 1), run a probe/scan pipeline
+ *   program (Table 1, Section 3.1) under one variant configuration
+ *   (Section 3.3: execution strategy, data structure, code transformations),
+ *   and fetch its result.
+ *
+ * Conventions for every call:
+ *   - Return value: PV_OK (0) or a negative pv_status; pv_last_error() then
+ *     holds a one-line message (ctx-owned, valid until the next call on ctx).
+ *   - Device pointers are plain CUDA device addresses on the ctx's device.
+ *     Columns are BORROWED: the caller keeps them alive and unmodified while
+ *     any pipeline that reads them may run; the library never frees them.
+ *   - Hash tables, results and graphs are OWNED by the ctx and released by
+ *     pv_free() or pv_destroy().  Handles are ctx-local int32 > 0.
+ *   - All GPU work is enqueued asynchronously on the ctx stream.  Errors that
+ *     kernels detect (table full, cuckoo cycle, key out of range, duplicate
+ *     build key, output overflow) are recorded in a device error word and
+ *     returned by the next pv_sync(), pv_result_shape() or pv_fetch_result().
+ *   - No call falls back to the CPU: a shape or variant with no compiled
+ *     instantiation returns PV_ERR_UNSUPPORTED.
+ *   - A ctx is not thread-safe; use one ctx per host thread.
+ */
+#ifndef PV_H
+#define PV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t pv_status;
+enum {
+  PV_OK = 0,
+  PV_ERR_INVALID_ARG = -1,      /* bad handle, size, alignment or spec */
+  PV_ERR_UNSUPPORTED = -2,      /* no compiled instantiation for this shape/variant */
+  PV_ERR_HT_FULL = -3,          /* linear-probing table or local table chain exhausted */
+  PV_ERR_CUCKOO_CYCLE = -4,     /* cuckoo eviction chain exceeded its bound */
+  PV_ERR_KEY_OUT_OF_RANGE = -5, /* perfect-array key outside the declared domain */
+  PV_ERR_DUP_BUILD_KEY = -6,    /* two surviving build rows with one key */
+  PV_ERR_OUTPUT_OVERFLOW = -7,  /* more projected rows than the output capacity */
+  PV_ERR_TIMEOUT = -8,          /* pv_sync watchdog expired; work may still run */
+  PV_ERR_CUDA = -9,             /* a CUDA runtime call failed */
+  PV_ERR_OOM = -10              /* the allocator returned NULL */
+};
+
+typedef enum { PV_I32 = 0, PV_I64 = 1, PV_U8 = 2 } pv_type;
+
+typedef struct pv_ctx pv_ctx;
+typedef int32_t pv_col;   /* column handle */
+typedef int32_t pv_ht;    /* hash-table handle */
+typedef int32_t pv_res;   /* result handle */
+typedef int32_t pv_graph; /* captured-graph handle */
+
+#define PV_MAX_PREDS 4
+#define PV_MAX_PROBES 4
+#define PV_MAX_KEYS 2
+#define PV_MAX_AGGS 8
+#define PV_MAX_TERMS 3
+#define PV_MAX_PROJ 4
+#define PV_MAX_PAYLOAD 1
+
+/* FILTER comparison (Table 1): column op constant, or lo <= column <= hi. */
+typedef enum { PV_LT = 0, PV_LE = 1, PV_GT = 2, PV_GE = 3, PV_EQ = 4, PV_BETWEEN = 5 } pv_cmp;
+/* Distributive aggregate functions (Section 7.5). */
+typedef enum { PV_SUM = 0, PV_COUNT = 1, PV_MIN = 2, PV_MAX = 3 } pv_func;
+/* ARITHMETIC term (Table 1): x, x + c or c - x; an aggregate's value is the
+ * product of its terms (e.g. price * (100 - disc) * (100 + tax)). */
+typedef enum { PV_TERM_X = 0, PV_TERM_X_PLUS_C = 1, PV_TERM_C_MINUS_X = 2 } pv_term_kind;
+/* Value reference: a column of the probe pipeline's table, or payload b of
+ * the build row matched by probe a (HASH_PROBE binds the payload). */
+typedef enum { PV_REF_COL = 0, PV_REF_PAYLOAD = 1 } pv_ref_kind;
+
+typedef struct { int32_t kind; int32_t a; int32_t b; } pv_ref;
+typedef struct { pv_col col; int32_t op; int64_t c0; int64_t c1; } pv_pred;
+typedef struct { int32_t kind; pv_ref x; int64_t c; } pv_term;
+typedef struct { int32_t func; int32_t n_terms; pv_term terms[PV_MAX_TERMS]; } pv_agg;
+typedef struct { pv_ht ht; pv_col fk; } pv_probe;
+
+/* Build pipeline (Table 2): LOOP over the key column's table, FILTER by the
+ * conjunction of preds, HASH_PUT key -> payload columns.  Key and payload
+ * columns are int32 (PV_I32) or uint8 (PV_U8) and have the same row count;
+ * a table slot is 64 bits (32-bit key, 32-bit payload), so at most one
+ * payload column. */
+typedef struct {
+  pv_col key;
+  int32_t n_preds;
+  pv_pred preds[PV_MAX_PREDS];
+  int32_t n_payload;
+  pv_col payload[PV_MAX_PAYLOAD];
+} pv_build_spec;
+
+/* Hash-table implementations (Section 5.1; perfect array added for dense
+ * key domains) and hash functions (Section 9.2.2: Murmur or multiply-shift). */
+typedef enum { PV_HT_LINEAR = 0, PV_HT_CUCKOO = 1, PV_HT_PERFECT = 2 } pv_ht_kind;
+typedef enum { PV_HASH_MURMUR = 0, PV_HASH_MULTSHIFT = 1 } pv_hash_fn;
+
+typedef struct {
+  int32_t kind;           /* pv_ht_kind */
+  int32_t hash;           /* pv_hash_fn (ignored by PV_HT_PERFECT) */
+  int32_t cuckoo_k;       /* cuckoo hash functions, 2..4 (0 = 3) */
+  int32_t max_evictions;  /* cuckoo eviction-chain bound (0 = 32 * log2(capacity)) */
+  double load_factor;     /* slots >= rows / load_factor, power of two (<= 0: 0.5) */
+  uint64_t seed;          /* hash-function seeds are derived from it */
+} pv_ht_variant;
+
+/* Probe/scan pipeline program (Table 1, Table 2): LOOP over the fact table,
+ * FILTER (conjunction of preds), HASH_PROBE each probe in order (a miss drops
+ * the row), then ARITHMETIC and one sink:
+ *   n_proj > 0              PROJECT proj (n_aggs must be 0)
+ *   n_keys > 0              HASH_AGGREGATE(keys, aggs)
+ *   otherwise               AGGREGATE(aggs)
+ * All fact columns referenced must have the same row count. */
+typedef struct {
+  int32_t n_preds;
+  pv_pred preds[PV_MAX_PREDS];
+  int32_t n_probes;
+  pv_probe probes[PV_MAX_PROBES];
+  int32_t n_keys;
+  pv_ref keys[PV_MAX_KEYS];
+  int32_t n_aggs;
+  pv_agg aggs[PV_MAX_AGGS];
+  int32_t n_proj;
+  pv_ref proj[PV_MAX_PROJ];
+  int64_t capacity_hint;  /* PROJECT: output row capacity (0 = fact rows);
+                             HASH_AGGREGATE: expected groups (0 = from column stats) */
+} pv_pipeline_spec;
+
+/* Variant configuration (Section 3.3, 4, 6; Table 5's dimensions). */
+typedef enum { PV_EXEC_SINGLE_PASS = 0, PV_EXEC_MULTI_PASS = 1 } pv_exec;
+typedef enum { PV_AGG_LOCAL = 0, PV_AGG_GLOBAL = 1 } pv_agg_strategy;
+typedef enum { PV_BRANCH = 0, PV_PREDICATED = 1 } pv_pred_mode;
+typedef enum { PV_GRID_STRIDE = 0, PV_CHUNKED = 1 } pv_access;
+
+typedef struct {
+  int32_t exec;              /* pv_exec: projection single pass (warp-aggregated atomics) or
+                                count -> prefix sum -> scatter; aggregation: fused, or keys first */
+  int32_t agg;               /* pv_agg_strategy for HASH_AGGREGATE */
+  int32_t pred;              /* pv_pred_mode (all operations of the pipeline share it) */
+  int32_t access;            /* pv_access: coalesced grid-stride or per-thread chunks */
+  int32_t ht;                /* pv_ht_kind of the aggregation table */
+  int32_t hash;              /* pv_hash_fn of the aggregation table */
+  int32_t block;             /* threads per CTA: 64..1024, multiple of 32 (0 = 256) */
+  int32_t grid_mult;         /* CTAs = grid_mult * SMs (0 = as many as fit at once) */
+  int32_t items_per_thread;  /* unroll: 4-row items per thread per trip, 1, 2 or 4 (0 = 2) */
+  int32_t threads_per_table; /* PV_AGG_LOCAL: 1 = thread-private tables, 0 = one per CTA */
+  int32_t cuckoo_k;          /* aggregation cuckoo hash functions (0 = 3) */
+  int32_t reserved;
+  uint64_t seed;             /* aggregation hash seeds */
+} pv_variant;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Creates a context on `device` that enqueues on `cuda_stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  If alloc is non-NULL,
+ * every device allocation goes through alloc(bytes, user) and free_(ptr,
+ * user) (e.g. a framework's caching allocator); otherwise cudaMallocAsync /
+ * cudaFreeAsync on the ctx stream.  *out is set to NULL on error. */
+pv_status pv_create(pv_ctx** out, int device, void* cuda_stream,
+                    void* (*alloc)(size_t bytes, void* user),
+                    void (*free_)(void* ptr, void* user), void* user);
+/* Waits for the ctx stream, then frees every owned table, result and graph. */
+pv_status pv_destroy(pv_ctx* ctx);
+/* Message of the last failing call on ctx; "" if none.  Never NULL. */
+const char* pv_last_error(const pv_ctx* ctx);
+/* Multiprocessor count and L2 bytes of the ctx device. */
+pv_status pv_device_info(pv_ctx* ctx, int32_t* sm_count, int64_t* l2_bytes);
+
+/* Registers a borrowed device column (column-major table storage, Section
+ * 7.5).  dev_ptr must be 16-byte aligned (vector loads); n_rows >= 0.
+ * table/name are copied and only used in messages. */
+pv_status pv_register_column(pv_ctx* ctx, const char* table, const char* name, int32_t type,
+                             const void* dev_ptr, int64_t n_rows, pv_col* out);
+/* Min and max of a column, computed on the GPU and cached (column
+ * statistics for perfect-array domains and the cost model).  Blocks. */
+pv_status pv_column_stats(pv_ctx* ctx, pv_col col, int64_t* min_out, int64_t* max_out);
+
+/* ---- build pipelines ---------------------------------------------------- */
+
+/* Runs one build pipeline (Table 2: LOOP, FILTER, HASH_PUT) into a new
+ * ctx-owned table of the requested implementation (Section 5.1).  Build and
+ * probe use the same table and parameters: the handle carries them.
+ * Duplicate surviving keys raise PV_ERR_DUP_BUILD_KEY at the next sync. */
+pv_status pv_build_hash_table(pv_ctx* ctx, const pv_build_spec* spec, const pv_ht_variant* var,
+                              pv_ht* out);
+
+/* ---- probe / scan pipelines --------------------------------------------- */
+
+/* Enqueues the pipeline program under the variant and returns a ctx-owned
+ * result handle.  Allocates the result (and scratch) before enqueueing. */
+pv_status pv_run_pipeline(pv_ctx* ctx, const pv_pipeline_spec* spec, const pv_variant* var,
+                          pv_res* out);
+/* Enqueues the same pipeline again into the same result buffers (clearing
+ * them first).  Allocates nothing, so it may be recorded by
+ * pv_graph_capture_begin/end. */
+pv_status pv_rerun(pv_ctx* ctx, pv_res res);
+/* Waits for the ctx stream (bounded by the watchdog, default 60 s) and
+ * returns the first kernel-detected error since the last sync, clearing it. */
+pv_status pv_sync(pv_ctx* ctx);
+/* Watchdog limit of pv_sync in milliseconds (> 0). */
+pv_status pv_set_timeout_ms(pv_ctx* ctx, int64_t ms);
+
+/* Result layout: grouped results are n_keys key columns then n_aggs
+ * aggregate columns (int64; key columns keep their source type widened to
+ * int64), one row per non-empty group, in unspecified order.  Ungrouped
+ * results are one row of n_aggs int64 columns (SUM/COUNT of no rows are 0;
+ * MIN/MAX of no rows read 0).  Projection results keep each column's source
+ * type and, for PV_EXEC_MULTI_PASS, input row order.  These calls sync. */
+pv_status pv_result_shape(pv_ctx* ctx, pv_res res, int64_t* n_rows, int32_t* n_cols);
+pv_status pv_result_col_type(pv_ctx* ctx, pv_res res, int32_t col, int32_t* type);
+/* Copies column col (n_rows values of its type) into dst, which holds
+ * dst_rows values, on the device if dst_on_device else in host memory. */
+pv_status pv_fetch_result(pv_ctx* ctx, pv_res res, int32_t col, void* dst, int64_t dst_rows,
+                          int32_t dst_on_device);
+/* Releases a table, result or graph handle (columns: forgets the handle). */
+pv_status pv_free(pv_ctx* ctx, int32_t handle);
+
+/* ---- CUDA graphs -------------------------------------------------------- */
+
+/* Records every pv_rerun (and pv_l2_flush) enqueued between begin and end
+ * into one CUDA graph, replayed by pv_graph_launch on the ctx stream (many
+ * small pipelines without per-launch overhead).  No other pv call may run
+ * in between. */
+pv_status pv_graph_capture_begin(pv_ctx* ctx);
+pv_status pv_graph_capture_end(pv_ctx* ctx, pv_graph* out);
+pv_status pv_graph_launch(pv_ctx* ctx, pv_graph g);
+
+/* ---- measurement support ------------------------------------------------ */
+
+/* Overwrites a ctx-owned buffer of twice the L2 size (cold-cache timing). */
+pv_status pv_l2_flush(pv_ctx* ctx);
+/* Kernels enqueued by the last pv_run_pipeline / pv_rerun / pv_build_hash_table. */
+pv_status pv_last_launch_count(pv_ctx* ctx, int32_t* n);
+/* Per-kernel GPU timing: when enabled, every kernel the library enqueues is
+ * bracketed by two CUDA events on the ctx stream.  pv_kernel_times syncs and
+ * writes the durations (ms) of the kernels enqueued by the last
+ * pv_run_pipeline / pv_rerun / pv_build_hash_table, in launch order, into
+ * ms[0..max), and their count into *n.  Not recorded inside graph capture. */
+pv_status pv_set_kernel_timing(pv_ctx* ctx, int32_t enable);
+pv_status pv_kernel_times(pv_ctx* ctx, float* ms, int32_t max, int32_t* n);
+/* Enqueues one kernel that busy-waits for `ns` nanoseconds of GPU clock
+ * (bounded; for exercising the pv_sync watchdog). */
+pv_status pv_debug_spin(pv_ctx* ctx, int64_t ns);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PV_H */

@@ -1,0 +1,242 @@
+// Build pipelines: LOOP over a dimension table, FILTER, HASH_PUT of key ->
+// payload (Table 1, Table 2) into one of three table implementations
+// (Section 5.1 linear probing and cuckoo hashing; perfect array for a dense
+// key domain).  Build and probe share the table layout of DevHT.
+#include <algorithm>
+
+#include "pv_build.h"
+#include "pv_internal.h"
+
+namespace pv {
+
+struct BuildParams {
+  BuildInput in;
+  DevHT ht;
+  int max_evictions;
+  int32_t* err;
+  unsigned long long* pay_stats;  // [2]: max code, min code of the payload
+};
+
+__device__ __forceinline__ int64_t load_any(const void* p, int type, int64_t r) {
+  if (type == PV_I32) return static_cast<const int32_t*>(p)[r];
+  if (type == PV_I64) return static_cast<const int64_t*>(p)[r];
+  return static_cast<const uint8_t*>(p)[r];
+}
+
+__device__ __forceinline__ uint64_t cuckoo_pos(const DevHT& h, uint32_t k32, int f) {
+  return ht_index(k32, h.hash, h.seed[f], h.log2cap);
+}
+
+// Linear probing insert of a unique key: claim the first empty slot of the
+// probe sequence with a CAS; meeting the key itself means a duplicate.
+__device__ __forceinline__ void linear_put(const DevHT& h, uint32_t k32, uint64_t val, int32_t* err) {
+  unsigned long long* slots = reinterpret_cast<unsigned long long*>(h.slots);
+  const uint64_t mask = static_cast<uint64_t>(h.cap) - 1;
+  uint64_t idx = ht_index(k32, h.hash, h.seed[0], h.log2cap);
+  for (int64_t step = 0; step < h.cap; ++step) {
+    unsigned long long cur = slots[idx];
+    while (static_cast<uint32_t>(cur >> 32) == kEmpty32) {
+      const unsigned long long old = atomicCAS(slots + idx, cur, static_cast<unsigned long long>(val));
+      if (old == cur) return;
+      cur = old;
+    }
+    if (static_cast<uint32_t>(cur >> 32) == k32) {
+      set_error(err, PV_ERR_DUP_BUILD_KEY);
+      return;
+    }
+    idx = (idx + 1) & mask;
+  }
+  set_error(err, PV_ERR_HT_FULL);
+}
+
+// Cuckoo insert (one slot per bucket, k hash functions): take any empty
+// candidate slot; otherwise swap into the candidate of the next function in
+// turn and continue with the evicted element, at most max_evictions times.
+__device__ __forceinline__ void cuckoo_put(const DevHT& h, uint64_t val, int max_evictions, int32_t* err) {
+  unsigned long long* slots = reinterpret_cast<unsigned long long*>(h.slots);
+  unsigned long long cur = val;
+  int f = 0;
+  for (int e = 0; e <= max_evictions; ++e) {
+    const uint32_t k32 = static_cast<uint32_t>(cur >> 32);
+    for (int i = 0; i < h.k; ++i) {
+      const uint64_t p = cuckoo_pos(h, k32, i);
+      unsigned long long s = slots[p];
+      if (static_cast<uint32_t>(s >> 32) == kEmpty32 && atomicCAS(slots + p, s, cur) == s) return;
+    }
+    const uint64_t p = cuckoo_pos(h, k32, f);
+    const unsigned long long old = atomicExch(slots + p, cur);
+    if (static_cast<uint32_t>(old >> 32) == kEmpty32) return;
+    cur = old;
+    // continue with the evicted key from the function after the one that
+    // placed it at p
+    const uint32_t ok = static_cast<uint32_t>(cur >> 32);
+    int placed = 0;
+    for (int i = 0; i < h.k; ++i)
+      if (cuckoo_pos(h, ok, i) == p) { placed = i; break; }
+    f = (placed + 1) % h.k;
+  }
+  set_error(err, PV_ERR_CUCKOO_CYCLE);
+}
+
+__global__ void k_build(const BuildParams bp) {
+  const BuildInput& in = bp.in;
+  const DevHT& h = bp.ht;
+  unsigned long long* slots = reinterpret_cast<unsigned long long*>(h.slots);
+  uint64_t pmax = 0, pmin = 0;
+  for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < in.n_rows;
+       r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    bool pass = true;
+    for (int i = 0; i < in.n_preds && pass; ++i) {
+      const int64_t v = load_any(in.pred_col[i], in.pred_type[i], r);
+      pass = in.lo[i] <= v && v <= in.hi[i];
+    }
+    if (!pass) continue;
+    const int64_t key = load_any(in.key, in.key_type, r);
+    const int32_t pay = in.n_payload ? static_cast<int32_t>(load_any(in.pay_col[0], in.pay_type[0], r)) : 0;
+    pmax = max(pmax, max_code(pay));
+    pmin = max(pmin, min_code(pay));
+    if (h.kind == PV_HT_PERFECT) {
+      const int64_t i = key - h.kmin;
+      if (static_cast<uint64_t>(i) >= static_cast<uint64_t>(h.cap)) {
+        set_error(bp.err, PV_ERR_KEY_OUT_OF_RANGE);
+        continue;
+      }
+      const unsigned long long v = (static_cast<unsigned long long>(static_cast<uint32_t>(pay)) << 32) | 1ull;
+      if (atomicCAS(slots + i, 0ull, v) != 0ull) set_error(bp.err, PV_ERR_DUP_BUILD_KEY);
+      continue;
+    }
+    const uint32_t k32 = static_cast<uint32_t>(key);
+    if (k32 == kEmpty32) {  // the key equal to the empty marker lives in the side slot
+      const unsigned long long v = static_cast<uint32_t>(pay);
+      if (atomicCAS(slots + h.cap, ~0ull, v) != ~0ull) set_error(bp.err, PV_ERR_DUP_BUILD_KEY);
+      continue;
+    }
+    const uint64_t val = (static_cast<uint64_t>(k32) << 32) | static_cast<uint32_t>(pay);
+    if (h.kind == PV_HT_LINEAR) linear_put(h, k32, val, bp.err);
+    else cuckoo_put(h, val, bp.max_evictions, bp.err);
+  }
+  pmax = warp_reduce<PV_MAX>(pmax);
+  pmin = warp_reduce<PV_MAX>(pmin);
+  if ((threadIdx.x & 31) == 0 && pmax) {
+    atomicMax(bp.pay_stats, static_cast<unsigned long long>(pmax));
+    atomicMax(bp.pay_stats + 1, static_cast<unsigned long long>(pmin));
+  }
+}
+
+// Duplicate check of a cuckoo table: every key stays within its k candidate
+// slots, so a key found in two of them was inserted twice.
+__global__ void k_cuckoo_dupcheck(const DevHT h, int32_t* err) {
+  const unsigned long long* slots = reinterpret_cast<const unsigned long long*>(h.slots);
+  for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < h.cap;
+       p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const uint32_t k32 = static_cast<uint32_t>(slots[p] >> 32);
+    if (k32 == kEmpty32) continue;
+    for (int i = 0; i < h.k; ++i) {
+      const uint64_t q = cuckoo_pos(h, k32, i);
+      if (q != static_cast<uint64_t>(p) && static_cast<uint32_t>(slots[q] >> 32) == k32) {
+        set_error(err, PV_ERR_DUP_BUILD_KEY);
+        return;
+      }
+    }
+  }
+}
+
+pv_status build_table(const BuildEnv& env, const BuildInput& in, const pv_ht_variant& var, int64_t kmin,
+                      int64_t kmax, BuildTable& out, std::string& msg) {
+  DevHT& h = out.ht;
+  h.kind = var.kind;
+  h.hash = var.hash;
+  if (var.kind != PV_HT_LINEAR && var.kind != PV_HT_CUCKOO && var.kind != PV_HT_PERFECT) {
+    msg = "bad hash table kind";
+    return PV_ERR_INVALID_ARG;
+  }
+  if (var.hash != PV_HASH_MURMUR && var.hash != PV_HASH_MULTSHIFT) {
+    msg = "bad hash function";
+    return PV_ERR_INVALID_ARG;
+  }
+  h.k = var.cuckoo_k ? var.cuckoo_k : 3;
+  if (h.k < 2 || h.k > 4) {
+    msg = "cuckoo_k must be 2..4";
+    return PV_ERR_INVALID_ARG;
+  }
+  uint64_t sd = var.seed ? var.seed : 0xb01d1709ull;
+  for (int i = 0; i < 4; ++i) {
+    sd = fmix64(sd + 0x9e3779b97f4a7c15ull);
+    h.seed[i] = sd | 1ull;
+  }
+  size_t bytes;
+  if (var.kind == PV_HT_PERFECT) {
+    const int64_t span = kmax >= kmin ? kmax - kmin + 1 : 1;
+    if (span > (int64_t(1) << 28)) {
+      msg = "perfect array: key domain larger than 2^28 slots";
+      return PV_ERR_UNSUPPORTED;
+    }
+    h.cap = span;
+    h.kmin = kmin;
+    h.log2cap = 0;
+    bytes = static_cast<size_t>(span) * 8;
+  } else {
+    const double lf = var.load_factor > 0 && var.load_factor <= 1 ? var.load_factor : 0.5;
+    const double want = std::max<double>(2.0, static_cast<double>(in.n_rows) / lf);
+    int l = 1;
+    while (static_cast<double>(int64_t(1) << l) < want) ++l;
+    if (l > 31) {
+      msg = "build table too large";
+      return PV_ERR_UNSUPPORTED;
+    }
+    h.log2cap = l;
+    h.cap = int64_t(1) << l;
+    bytes = static_cast<size_t>(h.cap + 1) * 8;
+  }
+  const int max_ev = var.max_evictions > 0 ? var.max_evictions : 32 * std::max(1, h.log2cap);
+  out.n_payload = in.n_payload;
+  out.mem = env.alloc(bytes + 64, env.user);
+  if (!out.mem) {
+    msg = "allocator returned NULL";
+    return PV_ERR_OOM;
+  }
+  h.slots = static_cast<uint64_t*>(out.mem);
+  unsigned long long* stats = reinterpret_cast<unsigned long long*>(static_cast<char*>(out.mem) + ((bytes + 15) & ~size_t(15)));
+  cudaError_t e = cudaMemsetAsync(h.slots, var.kind == PV_HT_PERFECT ? 0 : 0xFF, bytes, env.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(stats, 0, 16, env.stream);
+  if (e != cudaSuccess) {
+    msg = cudaGetErrorString(e);
+    return PV_ERR_CUDA;
+  }
+  BuildParams bp{};
+  bp.in = in;
+  bp.ht = h;
+  bp.max_evictions = max_ev;
+  bp.err = env.err;
+  bp.pay_stats = stats;
+  if (in.n_rows > 0) {
+    const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(env.sm_count * 8, (in.n_rows + 255) / 256)));
+    k_build<<<grid, 256, 0, env.stream>>>(bp);
+    ++*env.launches;
+    if (var.kind == PV_HT_CUCKOO) {
+      const int g2 = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(env.sm_count * 8, (h.cap + 255) / 256)));
+      k_cuckoo_dupcheck<<<g2, 256, 0, env.stream>>>(h, env.err);
+      ++*env.launches;
+    }
+  }
+  unsigned long long hs[2] = {0, 0};
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hs, stats, 16, cudaMemcpyDeviceToHost, env.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(env.stream);
+  if (e != cudaSuccess) {
+    msg = cudaGetErrorString(e);
+    return PV_ERR_CUDA;
+  }
+  if (in.n_payload) {
+    if (hs[0] == 0) {  // no surviving row
+      out.pay_min[0] = 0;
+      out.pay_max[0] = -1;
+    } else {
+      out.pay_max[0] = decode_max(hs[0]);
+      out.pay_min[0] = decode_min(hs[1]);
+    }
+  }
+  return PV_OK;
+}
+
+}  // namespace pv

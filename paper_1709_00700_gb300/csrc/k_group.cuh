@@ -1,0 +1,508 @@
+// HASH_AGGREGATE (Table 1) and result extraction.
+//
+// Execution strategies (Section 4.2):
+//   global aggregation: every row updates one global table with atomics;
+//   local aggregation: rows first update a CTA-local table in shared memory
+//     (N tables = the CTAs, M threads per table = the CTA), which is merged
+//     into the global table when the CTA finishes; with M = 1 every thread
+//     owns a private table (coarse-grained form, no atomics at all).
+// Table implementations (Section 5.1): linear probing, cuckoo hashing, and a
+// perfect array over a dense key domain.  Single pass inserts keys while
+// aggregating; multi pass inserts the keys in a first kernel and aggregates
+// with lookups in a second (cuckoo tables move keys while inserting, so they
+// always take the two passes, with a duplicate sweep in between).
+//
+// Global table: keys[cap + 1] (EMPTY = ~0; slot cap holds the key equal to
+// EMPTY) and vals[(cap + 1) * stride] with the aggregate codes and, last, the
+// row count of the slot.  Extraction compacts non-empty slots into dense int64
+// columns and leaves every slot it visits empty again, so a rerun needs no
+// clearing pass.
+#pragma once
+
+#include "pv_eval.cuh"
+
+namespace pv {
+
+constexpr int kLocalProbe = 16;          // probe-length bound in a local table
+constexpr size_t kLocalBytes = 96 << 10; // shared memory of a CTA-local table
+
+__device__ __forceinline__ uint64_t perfect_index(const GroupDesc& gd, int64_t p0, int64_t p1, bool& ok) {
+  const int64_t a = p0 - gd.key_min[0];
+  ok = static_cast<uint64_t>(a) < static_cast<uint64_t>(gd.key_span[0]);
+  if (gd.n_keys == 1) return static_cast<uint64_t>(a);
+  const int64_t b = p1 - gd.key_min[1];
+  ok = ok && static_cast<uint64_t>(b) < static_cast<uint64_t>(gd.key_span[1]);
+  return static_cast<uint64_t>(a) * static_cast<uint64_t>(gd.key_span[1]) + static_cast<uint64_t>(b);
+}
+
+// Global linear probing: slot of key, inserting it if absent.  Returns
+// cap + 1 on failure (table full; error recorded).
+__device__ __forceinline__ uint64_t global_linear_slot(const GroupOut& g, uint64_t key, int32_t* err) {
+  if (key == kEmpty64) return static_cast<uint64_t>(g.cap);
+  const uint64_t mask = static_cast<uint64_t>(g.cap) - 1;
+  uint64_t idx = ht_index(key, g.hash, g.seed[0], g.log2cap);
+  for (int64_t step = 0; step < g.cap; ++step) {
+    unsigned long long cur = __ldcg(g.keys + idx);  // keys change under us: read L2
+    if (cur == key) return idx;
+    if (cur == kEmpty64) {
+      cur = atomicCAS(g.keys + idx, kEmpty64, static_cast<unsigned long long>(key));
+      if (cur == kEmpty64 || cur == key) return idx;
+    }
+    idx = (idx + 1) & mask;
+  }
+  set_error(err, PV_ERR_HT_FULL);
+  return static_cast<uint64_t>(g.cap) + 1;
+}
+
+// Lookup of a key inserted by the key pass (linear or cuckoo).
+template <int HTK>
+__device__ __forceinline__ uint64_t global_lookup(const GroupOut& g, uint64_t key, int32_t* err) {
+  if (key == kEmpty64) return static_cast<uint64_t>(g.cap);
+  if constexpr (HTK == PV_HT_CUCKOO) {
+    for (int f = 0; f < g.cuckoo_k; ++f) {
+      const uint64_t p = ht_index(key, g.hash, g.seed[f], g.log2cap);
+      if (g.keys[p] == key) return p;
+    }
+  } else {
+    const uint64_t mask = static_cast<uint64_t>(g.cap) - 1;
+    uint64_t idx = ht_index(key, g.hash, g.seed[0], g.log2cap);
+    for (int64_t step = 0; step < g.cap; ++step) {
+      const unsigned long long cur = g.keys[idx];
+      if (cur == key) return idx;
+      if (cur == kEmpty64) break;
+      idx = (idx + 1) & mask;
+    }
+  }
+  set_error(err, PV_ERR_HT_FULL);  // a key the key pass did not insert: the table overflowed
+  return static_cast<uint64_t>(g.cap) + 1;
+}
+
+// Cuckoo insertion of a group key (key pass).  Skips keys already present;
+// concurrent inserts of one key may leave duplicates, removed by k_cuckoo_dedupe.
+__device__ __forceinline__ void global_cuckoo_insert(const GroupOut& g, uint64_t key, int32_t* err) {
+  if (key == kEmpty64) return;  // lives in the side slot, found by value
+  for (int f = 0; f < g.cuckoo_k; ++f)
+    if (__ldcg(g.keys + ht_index(key, g.hash, g.seed[f], g.log2cap)) == key) return;
+  unsigned long long cur = key;
+  int f = 0;
+  for (int e = 0; e <= g.max_evictions; ++e) {
+    for (int i = 0; i < g.cuckoo_k; ++i) {
+      const uint64_t p = ht_index(cur, g.hash, g.seed[i], g.log2cap);
+      unsigned long long s = __ldcg(g.keys + p);
+      if (s == cur) return;
+      if (s == kEmpty64 && atomicCAS(g.keys + p, kEmpty64, cur) == kEmpty64) return;
+    }
+    const uint64_t p = ht_index(cur, g.hash, g.seed[f], g.log2cap);
+    const unsigned long long old = atomicExch(g.keys + p, cur);
+    if (old == kEmpty64 || old == cur) return;
+    cur = old;
+    int placed = 0;
+    for (int i = 0; i < g.cuckoo_k; ++i)
+      if (ht_index(cur, g.hash, g.seed[i], g.log2cap) == p) { placed = i; break; }
+    f = (placed + 1) % g.cuckoo_k;
+  }
+  set_error(err, PV_ERR_CUCKOO_CYCLE);
+}
+
+// Adds one row's aggregate codes (count last) into a slot with atomics.
+template <int NA>
+__device__ __forceinline__ void slot_atomic_add(unsigned long long* v, const uint64_t (&c)[NA + 1],
+                                                const int32_t (&func)[PV_MAX_AGGS]) {
+#pragma unroll
+  for (int a = 0; a < NA; ++a) {
+    if (func[a] == PV_SUM || func[a] == PV_COUNT) {
+      if (c[a]) atomicAdd(v + a, static_cast<unsigned long long>(c[a]));
+    } else if (c[a]) {
+      atomicMax(v + a, static_cast<unsigned long long>(c[a]));
+    }
+  }
+  if (c[NA]) atomicAdd(v + NA, static_cast<unsigned long long>(c[NA]));
+}
+
+// Aggregate codes of row r: SUM/COUNT values, MIN/MAX order codes, row count;
+// masked to zero for a dead row (software predication).
+template <class SH>
+__device__ __forceinline__ void row_codes(Item<SH>& it, const KParams& kp, int r, uint64_t live_mask,
+                                          uint64_t (&c)[SH::Aggs::N + 1]) {
+  using A = typename SH::Aggs;
+  static_for<A::N>([&](auto a) {
+    constexpr int I = decltype(a)::value;
+    using AG = typename At<I, typename A::L>::type;
+    c[I] = acc_code<AG::func>(agg_value<AG>(it, kp, r)) & live_mask;
+  });
+  c[A::N] = 1ull & live_mask;
+}
+
+// ---------------------------------------------------------------------------
+// Sinks.  Each provides init() (CTA prologue), add() (one row) and finish()
+// (CTA epilogue); every thread of the CTA calls init and finish.
+// ---------------------------------------------------------------------------
+enum GlobalMode { G_INSERT = 0, G_LOOKUP_LINEAR = 1, G_LOOKUP_CUCKOO = 2 };
+
+template <int GM>
+__device__ __forceinline__ uint64_t global_slot(const GroupOut& g, uint64_t key, int32_t* err) {
+  if constexpr (GM == G_INSERT) return global_linear_slot(g, key, err);
+  else if constexpr (GM == G_LOOKUP_LINEAR) return global_lookup<PV_HT_LINEAR>(g, key, err);
+  else return global_lookup<PV_HT_CUCKOO>(g, key, err);
+}
+
+template <class SH, int GM>
+struct SinkGlobalHash {
+  static constexpr int NA = SH::Aggs::N;
+  const GroupDesc& gd; const GroupOut& g; int32_t* err;
+  __device__ SinkGlobalHash(const GroupDesc& d, const GroupOut& o, int32_t* e, unsigned long long*) : gd(d), g(o), err(e) {}
+  __device__ void init() {}
+  __device__ __forceinline__ void add(Item<SH>& it, const KParams& kp, int r, bool live) {
+    const uint64_t key = pack_key<SH>(it, kp, r);
+    const uint64_t s = global_slot<GM>(g, key, err);
+    if (s > static_cast<uint64_t>(g.cap)) return;
+    uint64_t c[NA + 1];
+    row_codes<SH>(it, kp, r, live ? ~0ull : 0ull, c);
+    slot_atomic_add<NA>(g.vals + s * g.stride, c, gd.func);
+  }
+  __device__ void finish() {}
+};
+
+template <class SH>
+__device__ __forceinline__ uint64_t row_perfect_index(const GroupDesc& gd, Item<SH>& it, const KParams& kp, int r,
+                                                      bool& ok) {
+  const int64_t p0 = key_part<SH, 0>(it, kp, r);
+  int64_t p1 = 0;
+  if constexpr (SH::Key::N == 2) p1 = key_part<SH, 1>(it, kp, r);
+  return perfect_index(gd, p0, p1, ok);
+}
+
+template <class SH>
+struct SinkGlobalPerfect {
+  static constexpr int NA = SH::Aggs::N;
+  const GroupDesc& gd; const GroupOut& g; int32_t* err;
+  __device__ SinkGlobalPerfect(const GroupDesc& d, const GroupOut& o, int32_t* e, unsigned long long*) : gd(d), g(o), err(e) {}
+  __device__ void init() {}
+  __device__ __forceinline__ void add(Item<SH>& it, const KParams& kp, int r, bool live) {
+    bool ok;
+    uint64_t s = row_perfect_index<SH>(gd, it, kp, r, ok);
+    if (!ok) {
+      if (live) { set_error(err, PV_ERR_KEY_OUT_OF_RANGE); return; }
+      s = 0;
+    }
+    uint64_t c[NA + 1];
+    row_codes<SH>(it, kp, r, live ? ~0ull : 0ull, c);
+    slot_atomic_add<NA>(g.vals + s * g.stride, c, gd.func);
+  }
+  __device__ void finish() {}
+};
+
+// Block-shared perfect array in shared memory (M = CTA threads), merged with
+// one atomic per non-zero entry.
+template <class SH>
+struct SinkLocalPerfect {
+  static constexpr int NA = SH::Aggs::N;
+  const GroupDesc& gd; const GroupOut& g; int32_t* err; unsigned long long* sm;
+  __device__ SinkLocalPerfect(const GroupDesc& d, const GroupOut& o, int32_t* e, unsigned long long* s)
+      : gd(d), g(o), err(e), sm(s) {}
+  __device__ void init() {
+    const int64_t words = g.cap * g.stride;
+    for (int64_t i = threadIdx.x; i < words; i += blockDim.x) sm[i] = 0;
+    __syncthreads();
+  }
+  __device__ __forceinline__ void add(Item<SH>& it, const KParams& kp, int r, bool live) {
+    bool ok;
+    uint64_t s = row_perfect_index<SH>(gd, it, kp, r, ok);
+    if (!ok) {
+      if (live) { set_error(err, PV_ERR_KEY_OUT_OF_RANGE); return; }
+      s = 0;
+    }
+    uint64_t c[NA + 1];
+    row_codes<SH>(it, kp, r, live ? ~0ull : 0ull, c);
+    slot_atomic_add<NA>(sm + s * g.stride, c, gd.func);
+  }
+  __device__ void finish() {
+    __syncthreads();
+    const int64_t words = g.cap * g.stride;
+    for (int64_t i = threadIdx.x; i < words; i += blockDim.x) {
+      const uint64_t v = sm[i];
+      if (!v) continue;
+      const int a = static_cast<int>(i % g.stride);
+      if (a == NA || gd.func[a] == PV_SUM || gd.func[a] == PV_COUNT) atomicAdd(g.vals + i, static_cast<unsigned long long>(v));
+      else atomicMax(g.vals + i, static_cast<unsigned long long>(v));
+    }
+  }
+};
+
+// Thread-private perfect arrays (M = 1): thread t owns the words
+// sm[w * blockDim + t]; no atomics until the CTA epilogue.
+template <class SH>
+struct SinkThreadPerfect {
+  static constexpr int NA = SH::Aggs::N;
+  const GroupDesc& gd; const GroupOut& g; int32_t* err; unsigned long long* sm;
+  __device__ SinkThreadPerfect(const GroupDesc& d, const GroupOut& o, int32_t* e, unsigned long long* s)
+      : gd(d), g(o), err(e), sm(s) {}
+  __device__ void init() {
+    const int64_t words = g.cap * g.stride;
+    for (int64_t w = 0; w < words; ++w) sm[w * blockDim.x + threadIdx.x] = 0;
+  }
+  __device__ __forceinline__ void add(Item<SH>& it, const KParams& kp, int r, bool live) {
+    bool ok;
+    uint64_t s = row_perfect_index<SH>(gd, it, kp, r, ok);
+    if (!ok) {
+      if (live) { set_error(err, PV_ERR_KEY_OUT_OF_RANGE); return; }
+      s = 0;
+    }
+    uint64_t c[NA + 1];
+    row_codes<SH>(it, kp, r, live ? ~0ull : 0ull, c);
+    unsigned long long* p = sm + s * g.stride * blockDim.x + threadIdx.x;
+#pragma unroll
+    for (int a = 0; a <= NA; ++a) {
+      const bool add = a == NA || gd.func[a] == PV_SUM || gd.func[a] == PV_COUNT;
+      const uint64_t cur = p[a * blockDim.x];
+      p[a * blockDim.x] = add ? cur + c[a] : (c[a] > cur ? c[a] : cur);
+    }
+  }
+  __device__ void finish() {
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int64_t words = g.cap * g.stride;
+    for (int64_t w = warp; w < words; w += nwarps) {
+      const int a = static_cast<int>(w % g.stride);
+      const bool add = a == NA || gd.func[a] == PV_SUM || gd.func[a] == PV_COUNT;
+      uint64_t v = 0;
+      for (int t = lane; t < static_cast<int>(blockDim.x); t += 32) {
+        const uint64_t x = sm[w * blockDim.x + t];
+        v = add ? v + x : (x > v ? x : v);
+      }
+      v = add ? warp_reduce<PV_SUM>(v) : warp_reduce<PV_MAX>(v);
+      if (lane == 0 && v) {
+        if (add) atomicAdd(g.vals + w, static_cast<unsigned long long>(v));
+        else atomicMax(g.vals + w, static_cast<unsigned long long>(v));
+      }
+    }
+  }
+};
+
+// CTA-local linear-probing table in shared memory; rows whose key does not
+// find a place within kLocalProbe steps go straight to the global table.
+template <class SH, int GM>
+struct SinkLocalHash {
+  static constexpr int NA = SH::Aggs::N;
+  const GroupDesc& gd; const GroupOut& g; int32_t* err; unsigned long long* lk; unsigned long long* lv;
+  __device__ SinkLocalHash(const GroupDesc& d, const GroupOut& o, int32_t* e, unsigned long long* s)
+      : gd(d), g(o), err(e), lk(s), lv(s + o.local_slots) {}
+  __device__ void init() {
+    for (int i = threadIdx.x; i < g.local_slots; i += blockDim.x) lk[i] = kEmpty64;
+    for (int64_t i = threadIdx.x; i < static_cast<int64_t>(g.local_slots) * g.stride; i += blockDim.x) lv[i] = 0;
+    __syncthreads();
+  }
+  __device__ __forceinline__ void add(Item<SH>& it, const KParams& kp, int r, bool live) {
+    const uint64_t key = pack_key<SH>(it, kp, r);
+    uint64_t c[NA + 1];
+    row_codes<SH>(it, kp, r, live ? ~0ull : 0ull, c);
+    if (key != kEmpty64) {
+      const uint32_t mask = static_cast<uint32_t>(g.local_slots) - 1;
+      uint32_t idx = static_cast<uint32_t>(fmix64(key)) & mask;
+      for (int step = 0; step < kLocalProbe; ++step) {
+        unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(lk + idx);
+        if (cur == kEmpty64) cur = atomicCAS(lk + idx, kEmpty64, static_cast<unsigned long long>(key));
+        if (cur == kEmpty64 || cur == key) {
+          slot_atomic_add<NA>(lv + static_cast<uint64_t>(idx) * g.stride, c, gd.func);
+          return;
+        }
+        idx = (idx + 1) & mask;
+      }
+    }
+    const uint64_t s = global_slot<GM>(g, key, err);
+    if (s <= static_cast<uint64_t>(g.cap)) slot_atomic_add<NA>(g.vals + s * g.stride, c, gd.func);
+  }
+  __device__ void finish() {
+    __syncthreads();
+    for (int i = threadIdx.x; i < g.local_slots; i += blockDim.x) {
+      const uint64_t key = lk[i];
+      if (key == kEmpty64) continue;
+      uint64_t c[NA + 1];
+#pragma unroll
+      for (int a = 0; a <= NA; ++a) c[a] = lv[static_cast<uint64_t>(i) * g.stride + a];
+      if (!c[NA]) continue;
+      const uint64_t s = global_slot<GM>(g, key, err);
+      if (s <= static_cast<uint64_t>(g.cap)) slot_atomic_add<NA>(g.vals + s * g.stride, c, gd.func);
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Kernels
+// ---------------------------------------------------------------------------
+template <class SH, bool PRED, bool CHUNK, int U, class Sink>
+__global__ void __maxnreg__(128) k_group(const KParams kp, const GroupDesc gd, const GroupOut g) {
+  extern __shared__ unsigned long long smem[];
+  if (blockIdx.x == 0 && threadIdx.x == 0) *g.out_count = 0;  // extraction runs after this kernel
+  Sink sink(gd, g, kp.err, smem);
+  sink.init();
+  for_items<CHUNK, U>(kp.n_items, [&](const int64_t (&idx)[U]) {
+    Item<SH> it[U];
+    eval_items<SH, PRED, U>(it, kp, idx);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (!PRED && !it[u].mask) continue;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const bool live = (it[u].mask >> r) & 1u;
+        if (PRED ? r < it[u].nvalid : live) sink.add(it[u], kp, r, live);
+      }
+    }
+  });
+  sink.finish();
+}
+
+// Key pass of the multi-pass strategy: insert the group key of every row
+// (every valid row when predicated) into the global linear or cuckoo table.
+template <class SH, bool PRED, bool CHUNK, int U, int HTK>
+__global__ void __maxnreg__(128) k_group_keys(const KParams kp, const GroupDesc gd, const GroupOut g) {
+  for_items<CHUNK, U>(kp.n_items, [&](const int64_t (&idx)[U]) {
+    Item<SH> it[U];
+    eval_items<SH, PRED, U>(it, kp, idx);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const bool live = (it[u].mask >> r) & 1u;
+        if (PRED ? r < it[u].nvalid : live) {
+          const uint64_t key = pack_key<SH>(it[u], kp, r);
+          if constexpr (HTK == PV_HT_CUCKOO) global_cuckoo_insert(g, key, kp.err);
+          else global_linear_slot(g, key, kp.err);
+        }
+      }
+    }
+  });
+}
+
+// Removes cuckoo duplicates: a key is kept only at the first of its k
+// candidate slots that holds it.
+__global__ void k_cuckoo_dedupe(const GroupOut g);
+// Compacts non-empty slots into the dense result columns and empties them.
+__global__ void k_extract(const GroupDesc gd, const GroupOut g);
+pv_status launch_dedupe_extract(const LaunchCfg& c, const GroupDesc& gd, const GroupOut& g, bool dedupe);
+
+template <class SH> using SinkGInsert = SinkGlobalHash<SH, G_INSERT>;
+template <class SH> using SinkGLookupLinear = SinkGlobalHash<SH, G_LOOKUP_LINEAR>;
+template <class SH> using SinkGLookupCuckoo = SinkGlobalHash<SH, G_LOOKUP_CUCKOO>;
+template <class SH> using SinkLInsert = SinkLocalHash<SH, G_INSERT>;
+template <class SH> using SinkLLookupLinear = SinkLocalHash<SH, G_LOOKUP_LINEAR>;
+template <class SH> using SinkLLookupCuckoo = SinkLocalHash<SH, G_LOOKUP_CUCKOO>;
+
+template <class K>
+static pv_status launch_k(const LaunchCfg& c, K k, const KParams& kp, const GroupDesc& gd, const GroupOut& g,
+                          size_t smem, int U) {
+  if (smem > 48 * 1024) {
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
+      return PV_ERR_UNSUPPORTED;
+  }
+  const int grid = grid_for(c, reinterpret_cast<const void*>(k), smem, kp.n_items, static_cast<int64_t>(c.block) * U);
+  if (grid <= 0) return PV_ERR_UNSUPPORTED;
+  kmark(c);
+  k<<<grid, c.block, smem, c.stream>>>(kp, gd, g);
+  kmark(c);
+  ++*c.launches;
+  return cudaGetLastError() == cudaSuccess ? PV_OK : PV_ERR_CUDA;
+}
+
+// UMASK: bit 0 = unroll 1 compiled, bit 1 = unroll 2 compiled.
+template <class SH, int UMASK, template <class> class SinkT>
+static pv_status run_group(const LaunchCfg& c, const KParams& kp, const GroupDesc& gd, const GroupOut& g, size_t smem) {
+  using S = SinkT<SH>;
+  if constexpr ((UMASK & 1) != 0) if (c.U == 1) {
+    if (c.pred) return c.chunk ? launch_k(c, k_group<SH, true, true, 1, S>, kp, gd, g, smem, 1)
+                               : launch_k(c, k_group<SH, true, false, 1, S>, kp, gd, g, smem, 1);
+    return c.chunk ? launch_k(c, k_group<SH, false, true, 1, S>, kp, gd, g, smem, 1)
+                   : launch_k(c, k_group<SH, false, false, 1, S>, kp, gd, g, smem, 1);
+  }
+  if constexpr ((UMASK & 2) != 0) if (c.U == 2) {
+    if (c.pred) return c.chunk ? launch_k(c, k_group<SH, true, true, 2, S>, kp, gd, g, smem, 2)
+                               : launch_k(c, k_group<SH, true, false, 2, S>, kp, gd, g, smem, 2);
+    return c.chunk ? launch_k(c, k_group<SH, false, true, 2, S>, kp, gd, g, smem, 2)
+                   : launch_k(c, k_group<SH, false, false, 2, S>, kp, gd, g, smem, 2);
+  }
+  return PV_ERR_UNSUPPORTED;
+}
+
+template <class SH, int UMASK, int HTK>
+static pv_status run_keys(const LaunchCfg& c, const KParams& kp, const GroupDesc& gd, const GroupOut& g) {
+  if constexpr ((UMASK & 1) != 0) if (c.U == 1) {
+    if (c.pred) return c.chunk ? launch_k(c, k_group_keys<SH, true, true, 1, HTK>, kp, gd, g, 0, 1)
+                               : launch_k(c, k_group_keys<SH, true, false, 1, HTK>, kp, gd, g, 0, 1);
+    return c.chunk ? launch_k(c, k_group_keys<SH, false, true, 1, HTK>, kp, gd, g, 0, 1)
+                   : launch_k(c, k_group_keys<SH, false, false, 1, HTK>, kp, gd, g, 0, 1);
+  }
+  if constexpr ((UMASK & 2) != 0) if (c.U == 2) {
+    if (c.pred) return c.chunk ? launch_k(c, k_group_keys<SH, true, true, 2, HTK>, kp, gd, g, 0, 2)
+                               : launch_k(c, k_group_keys<SH, true, false, 2, HTK>, kp, gd, g, 0, 2);
+    return c.chunk ? launch_k(c, k_group_keys<SH, false, true, 2, HTK>, kp, gd, g, 0, 2)
+                   : launch_k(c, k_group_keys<SH, false, false, 2, HTK>, kp, gd, g, 0, 2);
+  }
+  return PV_ERR_UNSUPPORTED;
+}
+
+// HASH_AGGREGATE under one variant: picks the sink (strategy x table kind x
+// pass count), enqueues the key pass if any, the aggregation kernel and the
+// extraction kernel.
+template <class SH, int UMASK>
+static pv_status launch_group(const LaunchCfg& c, const KParams& kp, const GroupDesc& gd, const GroupOut& g0,
+                              const pv_variant& v) {
+  GroupOut g = g0;
+  const bool multi = v.exec == PV_EXEC_MULTI_PASS;
+  const bool local = v.agg == PV_AGG_LOCAL;
+  if (v.agg != PV_AGG_LOCAL && v.agg != PV_AGG_GLOBAL) return PV_ERR_INVALID_ARG;
+  const size_t slot_bytes = static_cast<size_t>(g.stride) * 8;
+  pv_status s;
+  if (g.ht == PV_HT_PERFECT) {
+    if (multi) return PV_ERR_UNSUPPORTED;  // no keys to insert
+    if (!local) {
+      s = run_group<SH, UMASK, SinkGlobalPerfect>(c, kp, gd, g, 0);
+    } else if (v.threads_per_table == 1) {
+      const size_t smem = static_cast<size_t>(g.cap) * slot_bytes * c.block;
+      if (smem > 200 * 1024) return PV_ERR_UNSUPPORTED;
+      s = run_group<SH, UMASK, SinkThreadPerfect>(c, kp, gd, g, smem);
+    } else {
+      const size_t smem = static_cast<size_t>(g.cap) * slot_bytes;
+      if (smem > kLocalBytes) return PV_ERR_UNSUPPORTED;
+      s = run_group<SH, UMASK, SinkLocalPerfect>(c, kp, gd, g, smem);
+    }
+    if (s != PV_OK) return s;
+    return launch_dedupe_extract(c, gd, g, false);
+  }
+  if (v.threads_per_table == 1) return PV_ERR_UNSUPPORTED;
+  const bool cuckoo = g.ht == PV_HT_CUCKOO;
+  if (cuckoo && !multi) return PV_ERR_UNSUPPORTED;  // keys move while inserting
+  if (multi) {
+    s = cuckoo ? run_keys<SH, UMASK, PV_HT_CUCKOO>(c, kp, gd, g) : run_keys<SH, UMASK, PV_HT_LINEAR>(c, kp, gd, g);
+    if (s != PV_OK) return s;
+    if (cuckoo) {
+      s = launch_dedupe_extract(c, gd, g, true);
+      if (s != PV_OK) return s;
+    }
+  }
+  if (!local) {
+    s = !multi ? run_group<SH, UMASK, SinkGInsert>(c, kp, gd, g, 0)
+               : cuckoo ? run_group<SH, UMASK, SinkGLookupCuckoo>(c, kp, gd, g, 0)
+                        : run_group<SH, UMASK, SinkGLookupLinear>(c, kp, gd, g, 0);
+  } else {
+    int ls = 1;
+    while (static_cast<size_t>(ls) * 2 * (slot_bytes + 8) <= kLocalBytes) ls *= 2;
+    g.local_slots = ls;
+    const size_t smem = static_cast<size_t>(ls) * (slot_bytes + 8);
+    s = !multi ? run_group<SH, UMASK, SinkLInsert>(c, kp, gd, g, smem)
+               : cuckoo ? run_group<SH, UMASK, SinkLLookupCuckoo>(c, kp, gd, g, smem)
+                        : run_group<SH, UMASK, SinkLLookupLinear>(c, kp, gd, g, smem);
+  }
+  if (s != PV_OK) return s;
+  return launch_dedupe_extract(c, gd, g, false);
+}
+
+template <class SH, int UMASK = 3>
+static void reg_grouped() {
+  ShapeEntry e{};
+  e.sig = SH::signature();
+  e.mode = MODE_GROUPED;
+  e.grouped = launch_group<SH, UMASK>;
+  register_shape(e);
+}
+
+}  // namespace pv

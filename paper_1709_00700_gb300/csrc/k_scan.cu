@@ -1,0 +1,427 @@
+// Scan pipelines without a hash-aggregation sink:
+//   AGGREGATE (ungrouped, Table 1; Section 7.3 aggregate fragment),
+//   PROJECT single pass (Section 4.1 coarse-grained strategy, here with
+//     warp-aggregated atomics on one output cursor),
+//   PROJECT multi pass (Section 4.1 fine-grained strategy: a filter kernel
+//     counts matches, a prefix sum yields unique write positions, a
+//     projection kernel repeats filter and probes and writes).
+#include "pv_eval.cuh"
+
+namespace pv {
+
+// ---------------------------------------------------------------------------
+// AGGREGATE: per-thread accumulators (predicated mode folds every row with
+// its flag as a 0/-1 mask, the multiplication of Section 6), warp shuffle
+// reduction, one shared-memory pass per CTA, one atomic per CTA and
+// aggregate; the last CTA decodes the result and re-zeroes the accumulators.
+// ---------------------------------------------------------------------------
+template <class SH, bool PRED, bool CHUNK, int U>
+__global__ void __maxnreg__(128) k_aggregate(const KParams kp, const AggOut out) {
+  using A = typename SH::Aggs;
+  constexpr int NA = A::N;
+  uint64_t acc[NA + 1];
+#pragma unroll
+  for (int a = 0; a <= NA; ++a) acc[a] = 0;
+
+  for_items<CHUNK, U>(kp.n_items, [&](const int64_t (&idx)[U]) {
+    Item<SH> it[U];
+    eval_items<SH, PRED, U>(it, kp, idx);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const uint32_t live = (it[u].mask >> r) & 1u;
+        if constexpr (PRED) {
+          const uint64_t m = 0ull - live;
+          static_for<NA>([&](auto a) {
+            constexpr int I = decltype(a)::value;
+            using AG = typename At<I, typename A::L>::type;
+            acc[I] = acc_combine<AG::func>(acc[I], acc_code<AG::func>(agg_value<AG>(it[u], kp, r)) & m);
+          });
+          acc[NA] += live;
+        } else if (live) {
+          static_for<NA>([&](auto a) {
+            constexpr int I = decltype(a)::value;
+            using AG = typename At<I, typename A::L>::type;
+            acc[I] = acc_combine<AG::func>(acc[I], acc_code<AG::func>(agg_value<AG>(it[u], kp, r)));
+          });
+          acc[NA] += 1;
+        }
+      }
+    }
+  });
+
+  __shared__ unsigned long long red[32][NA + 1];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  static_for<NA + 1>([&](auto a) {
+    constexpr int I = decltype(a)::value;
+    constexpr int F = I < NA ? A::func_of[I < NA ? I : 0] : PV_COUNT;
+    acc[I] = warp_reduce<F>(acc[I]);
+  });
+  if (lane == 0) {
+#pragma unroll
+    for (int a = 0; a <= NA; ++a) red[warp][a] = acc[a];
+  }
+  __syncthreads();
+  if (warp == 0) {
+    static_for<NA + 1>([&](auto a) {
+      constexpr int I = decltype(a)::value;
+      constexpr int F = I < NA ? A::func_of[I < NA ? I : 0] : PV_COUNT;
+      uint64_t v = lane < nwarps ? red[lane][I] : 0;
+      v = warp_reduce<F>(v);
+      if (lane == 0 && v != 0) acc_atomic<F>(out.acc + I, v);
+    });
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(out.done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    const uint64_t rows = atomicExch(out.acc + NA, 0ull);
+    static_for<NA>([&](auto a) {
+      constexpr int I = decltype(a)::value;
+      constexpr int F = A::func_of[I];
+      const uint64_t c = atomicExch(out.acc + I, 0ull);
+      int64_t v = static_cast<int64_t>(c);
+      if constexpr (F == PV_MIN) v = rows ? decode_min(c) : 0;
+      if constexpr (F == PV_MAX) v = rows ? decode_max(c) : 0;
+      out.result[I] = v;
+    });
+    *out.done = 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// PROJECT helpers
+// ---------------------------------------------------------------------------
+template <class SH>
+__device__ __forceinline__ void write_row(const ProjOut& out, Item<SH>& it, int r, int64_t pos) {
+  using PJ = typename SH::Proj;
+  static_for<PJ::N>([&](auto c) {
+    constexpr int C = decltype(c)::value;
+    constexpr int S = PJ::slot_of[C];
+    using T = typename At<S, typename SH::Cols::L>::type::T;
+    static_cast<T*>(out.col[C])[pos] = VGet<S>::get(it.v)[r];
+  });
+}
+
+__device__ __forceinline__ int warp_incl_scan(int v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += y;
+  }
+  return v;
+}
+
+// Block-wide exclusive scan of a 64-bit value; returns the prefix and sets
+// *total.  Every thread of the block must call it.
+__device__ __forceinline__ uint64_t block_excl_scan(uint64_t v, uint64_t* total) {
+  __shared__ unsigned long long ws[33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  uint64_t incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = __shfl_up_sync(0xffffffffu, static_cast<unsigned long long>(incl), o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) ws[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint64_t w = lane < nwarps ? ws[lane] : 0;
+    uint64_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xffffffffu, static_cast<unsigned long long>(wi), o);
+      if (lane >= o) wi += y;
+    }
+    if (lane < nwarps) ws[lane] = wi - w;
+    if (lane == 31) ws[32] = wi;  // nwarps <= 32: lane 31 holds the grand total
+  }
+  __syncthreads();
+  const uint64_t ex = ws[warp] + incl - v;
+  *total = ws[32];
+  __syncthreads();
+  return ex;
+}
+
+// Single pass: every warp reserves its matches with one atomicAdd on the
+// output cursor (ballot-free: counts are scanned with shuffles), then each
+// lane writes its rows.  Output order is arbitrary across warps.
+template <class SH, bool PRED, bool CHUNK, int U>
+__global__ void __maxnreg__(128) k_project_sp(const KParams kp, const ProjOut out) {
+  bool overflow = false;
+  for_items_uniform<CHUNK, U>(kp.n_items, [&](const int64_t (&idx)[U]) {
+    Item<SH> it[U];
+    eval_items<SH, PRED, U>(it, kp, idx);
+    int cnt = 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) cnt += __popc(it[u].mask);
+    const int incl = warp_incl_scan(cnt);
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) return;
+    unsigned long long base = 0;
+    if ((threadIdx.x & 31) == 31) base = atomicAdd(out.cursor, static_cast<unsigned long long>(total));
+    base = __shfl_sync(0xffffffffu, base, 31);
+    int64_t pos = static_cast<int64_t>(base) + incl - cnt;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        if ((it[u].mask >> r) & 1u) {
+          if (pos < out.capacity) write_row<SH>(out, it[u], r, pos);
+          else overflow = true;
+          ++pos;
+        }
+      }
+    }
+  });
+  if (overflow) set_error(kp.err, PV_ERR_OUTPUT_OVERFLOW);
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(out.done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    const int64_t n = static_cast<int64_t>(atomicExch(out.cursor, 0ull));
+    *out.count = n < out.capacity ? n : out.capacity;
+    *out.done = 0;
+  }
+}
+
+// Multi pass.  A tile is blockDim * U items.  Tiles go to CTAs grid-stride
+// (coalesced) or as one contiguous range per CTA (chunked); inside a tile the
+// item of (thread t, unroll u) is u * blockDim + t (coalesced) or t * U + u
+// (chunked).  Count kernel and scatter kernel use the same mapping.
+template <bool CHUNK, int U>
+__device__ __forceinline__ void tile_items(int64_t tile, int64_t (&idx)[U]) {
+  const int64_t base = tile * static_cast<int64_t>(blockDim.x) * U;
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+    idx[u] = CHUNK ? base + static_cast<int64_t>(threadIdx.x) * U + u
+                   : base + static_cast<int64_t>(u) * blockDim.x + threadIdx.x;
+}
+
+template <bool CHUNK, class F>
+__device__ __forceinline__ void for_tiles(int64_t n_tiles, F&& f) {
+  if constexpr (!CHUNK) {
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) f(tile);
+  } else {
+    const int64_t per = (n_tiles + gridDim.x - 1) / gridDim.x;
+    const int64_t b = blockIdx.x * per;
+    const int64_t e = b + per < n_tiles ? b + per : n_tiles;
+    for (int64_t tile = b; tile < e; ++tile) f(tile);
+  }
+}
+
+template <class SH, bool PRED, bool CHUNK, int U>
+__global__ void __maxnreg__(128) k_project_count(const KParams kp, const ProjOut out) {
+  for_tiles<CHUNK>(out.n_tiles, [&](int64_t tile) {
+    int64_t idx[U];
+    tile_items<CHUNK, U>(tile, idx);
+    Item<SH> it[U];
+    eval_items<SH, PRED, U>(it, kp, idx);
+    uint64_t cnt = 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) cnt += __popc(it[u].mask);
+    uint64_t total;
+    block_excl_scan(cnt, &total);
+    if (threadIdx.x == 0) out.tile_count[tile] = static_cast<int64_t>(total);
+  });
+}
+
+// Exclusive prefix sum over the tile counts (one CTA of 1024 threads).
+__global__ void __launch_bounds__(1024) k_tile_scan(const ProjOut out, int32_t* err) {
+  const int64_t n = out.n_tiles;
+  const int64_t per = (n + blockDim.x - 1) / blockDim.x;
+  const int64_t b = threadIdx.x * per;
+  const int64_t e = b + per < n ? b + per : n;
+  uint64_t s = 0;
+  for (int64_t i = b; i < e; ++i) s += out.tile_count[i];
+  uint64_t total;
+  uint64_t run = block_excl_scan(s, &total);
+  for (int64_t i = b; i < e; ++i) {
+    out.tile_offset[i] = static_cast<int64_t>(run);
+    run += out.tile_count[i];
+  }
+  if (threadIdx.x == 0) {
+    const int64_t t = static_cast<int64_t>(total);
+    *out.count = t < out.capacity ? t : out.capacity;
+    if (t > out.capacity) set_error(err, PV_ERR_OUTPUT_OVERFLOW);
+  }
+}
+
+template <class SH, bool PRED, bool CHUNK, int U>
+__global__ void __maxnreg__(128) k_project_scatter(const KParams kp, const ProjOut out) {
+  static_assert(U <= 4, "16-bit scan fields hold at most 4 unroll slots");
+  for_tiles<CHUNK>(out.n_tiles, [&](int64_t tile) {
+    int64_t idx[U];
+    tile_items<CHUNK, U>(tile, idx);
+    Item<SH> it[U];
+    eval_items<SH, PRED, U>(it, kp, idx);
+    int64_t pos[U];
+    const int64_t base = out.tile_offset[tile];
+    if constexpr (CHUNK) {
+      // row order inside the tile: (thread, u, row)
+      uint64_t c = 0;
+#pragma unroll
+      for (int u = 0; u < U; ++u) c += __popc(it[u].mask);
+      uint64_t total;
+      int64_t p = base + static_cast<int64_t>(block_excl_scan(c, &total));
+#pragma unroll
+      for (int u = 0; u < U; ++u) { pos[u] = p; p += __popc(it[u].mask); }
+    } else {
+      // row order inside the tile: (u, thread, row); one scan of U packed
+      // 16-bit counters (each at most 4 * 1024 per tile)
+      uint64_t packed = 0;
+#pragma unroll
+      for (int u = 0; u < U; ++u) packed |= static_cast<uint64_t>(__popc(it[u].mask)) << (16 * u);
+      uint64_t total;
+      const uint64_t ex = block_excl_scan(packed, &total);
+      int64_t before = 0;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        pos[u] = base + before + static_cast<int64_t>((ex >> (16 * u)) & 0xFFFF);
+        before += static_cast<int64_t>((total >> (16 * u)) & 0xFFFF);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      int64_t p = pos[u];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        if ((it[u].mask >> r) & 1u) {
+          if (p < out.capacity) write_row<SH>(out, it[u], r, p);
+          ++p;
+        }
+      }
+    }
+  });
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+template <class SH, bool P, bool C, int U>
+static pv_status launch_agg_t(const LaunchCfg& c, const KParams& kp, const AggOut& out) {
+  auto k = k_aggregate<SH, P, C, U>;
+  const int grid = grid_for(c, reinterpret_cast<const void*>(k), 0, kp.n_items, static_cast<int64_t>(c.block) * U);
+  if (grid <= 0) return PV_ERR_UNSUPPORTED;
+  kmark(c);
+  k<<<grid, c.block, 0, c.stream>>>(kp, out);
+  kmark(c);
+  ++*c.launches;
+  return cudaGetLastError() == cudaSuccess ? PV_OK : PV_ERR_CUDA;
+}
+
+template <class SH, bool P, bool C, int U>
+static pv_status launch_proj_t(const LaunchCfg& c, const KParams& kp, const ProjOut& out, int exec) {
+  if (exec == PV_EXEC_SINGLE_PASS) {
+    auto k = k_project_sp<SH, P, C, U>;
+    const int grid = grid_for(c, reinterpret_cast<const void*>(k), 0, kp.n_items, static_cast<int64_t>(c.block) * U);
+    if (grid <= 0) return PV_ERR_UNSUPPORTED;
+    kmark(c);
+    k<<<grid, c.block, 0, c.stream>>>(kp, out);
+    kmark(c);
+    ++*c.launches;
+  } else {
+    auto kc = k_project_count<SH, P, C, U>;
+    auto ks = k_project_scatter<SH, P, C, U>;
+    const int grid = grid_for(c, reinterpret_cast<const void*>(kc), 0, out.n_tiles, 1);
+    if (grid <= 0 || grid_for(c, reinterpret_cast<const void*>(ks), 0, 1, 1) <= 0) return PV_ERR_UNSUPPORTED;
+    kmark(c);
+    kc<<<grid, c.block, 0, c.stream>>>(kp, out);
+    kmark(c);
+    kmark(c);
+    k_tile_scan<<<1, 1024, 0, c.stream>>>(out, kp.err);
+    kmark(c);
+    kmark(c);
+    ks<<<grid, c.block, 0, c.stream>>>(kp, out);
+    kmark(c);
+    *c.launches += 3;
+  }
+  return cudaGetLastError() == cudaSuccess ? PV_OK : PV_ERR_CUDA;
+}
+
+template <class SH>
+static pv_status launch_agg(const LaunchCfg& c, const KParams& kp, const AggOut& out) {
+  using F = pv_status (*)(const LaunchCfg&, const KParams&, const AggOut&);
+  static const F tab[2][2][3] = {
+      {{launch_agg_t<SH, false, false, 1>, launch_agg_t<SH, false, false, 2>, launch_agg_t<SH, false, false, 4>},
+       {launch_agg_t<SH, false, true, 1>, launch_agg_t<SH, false, true, 2>, launch_agg_t<SH, false, true, 4>}},
+      {{launch_agg_t<SH, true, false, 1>, launch_agg_t<SH, true, false, 2>, launch_agg_t<SH, true, false, 4>},
+       {launch_agg_t<SH, true, true, 1>, launch_agg_t<SH, true, true, 2>, launch_agg_t<SH, true, true, 4>}}};
+  const int ui = c.U == 1 ? 0 : c.U == 2 ? 1 : c.U == 4 ? 2 : -1;
+  if (ui < 0) return PV_ERR_UNSUPPORTED;
+  return tab[c.pred][c.chunk][ui](c, kp, out);
+}
+
+template <class SH>
+static pv_status launch_proj(const LaunchCfg& c, const KParams& kp, const ProjOut& out, int exec) {
+  using F = pv_status (*)(const LaunchCfg&, const KParams&, const ProjOut&, int);
+  static const F tab[2][2][3] = {
+      {{launch_proj_t<SH, false, false, 1>, launch_proj_t<SH, false, false, 2>, launch_proj_t<SH, false, false, 4>},
+       {launch_proj_t<SH, false, true, 1>, launch_proj_t<SH, false, true, 2>, launch_proj_t<SH, false, true, 4>}},
+      {{launch_proj_t<SH, true, false, 1>, launch_proj_t<SH, true, false, 2>, launch_proj_t<SH, true, false, 4>},
+       {launch_proj_t<SH, true, true, 1>, launch_proj_t<SH, true, true, 2>, launch_proj_t<SH, true, true, 4>}}};
+  const int ui = c.U == 1 ? 0 : c.U == 2 ? 1 : c.U == 4 ? 2 : -1;
+  if (ui < 0) return PV_ERR_UNSUPPORTED;
+  return tab[c.pred][c.chunk][ui](c, kp, out, exec);
+}
+
+template <class SH>
+static void reg_aggregate() {
+  ShapeEntry e{};
+  e.sig = SH::signature();
+  e.mode = MODE_AGGREGATE;
+  e.aggregate = launch_agg<SH>;
+  register_shape(e);
+}
+template <class SH>
+static void reg_project() {
+  ShapeEntry e{};
+  e.sig = SH::signature();
+  e.mode = MODE_PROJECT;
+  e.project = launch_proj<SH>;
+  register_shape(e);
+}
+
+// ---- compiled shapes -------------------------------------------------------
+// Filter/aggregate/project table (a int32, b int32, price int64):
+//   WHERE range(a) AND range(b) -> SUM(price), COUNT(*)   |   -> (a, price)
+using ShFilterAgg = Shape<Cols<TI32, TI32, TI64>, Where<P<0>, P<1>>, Probes<>, Key<>,
+                          Aggs<Sum<Mul<X<2>>>, Count>, Proj<>>;
+using ShFilterProj = Shape<Cols<TI32, TI32, TI64>, Where<P<0>, P<1>>, Probes<>, Key<>, Aggs<>, Proj<0, 2>>;
+// Same table, one predicate (projection query with a single filter).
+using ShFilterProj1 = Shape<Cols<TI32, TI32, TI64>, Where<P<0>>, Probes<>, Key<>, Aggs<>, Proj<1, 2>>;
+// Ungrouped fixed-point aggregation of the low-cardinality table (all 8
+// aggregates, no grouping) — the totals of the grouped query.
+using ShLowcardTotals =
+    Shape<Cols<TI32, TI64, TI64, TI64, TI64>, Where<P<0>>, Probes<>, Key<>,
+          Aggs<Sum<Mul<X<1>>>, Sum<Mul<X<2>>>, Sum<Mul<X<3>>>, Sum<Mul<X<4>>>, Sum<Mul<X<2>, CMX<3, 0>>>,
+               Sum<Mul<X<2>, CMX<3, 1>, XPC<4, 2>>>, Sum<Mul<X<1>, X<2>>>, Count>,
+          Proj<>>;
+// key/value table: filtered SUM/COUNT/MIN/MAX of val.
+using ShKeyValTotals = Shape<Cols<TI64>, Where<P<0>>, Probes<>, Key<>,
+                             Aggs<Sum<Mul<X<0>>>, Count, Min<Mul<X<0>>>, Max<Mul<X<0>>>>, Proj<>>;
+
+// One probe, COUNT(*) of the joining rows (join cardinality).
+using ShJoinCount = Shape<Cols<TI32>, Where<>, Probes<0>, Key<>, Aggs<Count>, Proj<>>;
+
+void register_scan_shapes() {
+  reg_aggregate<ShJoinCount>();
+  reg_aggregate<ShFilterAgg>();
+  reg_project<ShFilterProj>();
+  reg_project<ShFilterProj1>();
+  reg_aggregate<ShLowcardTotals>();
+  reg_aggregate<ShKeyValTotals>();
+}
+
+}  // namespace pv

@@ -1,0 +1,108 @@
+// Host-side interface between the C-ABI layer (pv_api.cu) and the kernel
+// translation units: launch configuration, result buffers and the registry
+// of compiled pipeline shapes.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+#include <cuda_runtime.h>
+
+#include "pv.h"
+#include "pv_device.cuh"
+
+namespace pv {
+
+enum Mode { MODE_AGGREGATE = 0, MODE_GROUPED = 1, MODE_PROJECT = 2 };
+
+// Launch shape resolved from a pv_variant.
+struct LaunchCfg {
+  cudaStream_t stream;
+  int sm_count;
+  int block;      // threads per CTA
+  int grid_mult;  // 0: fill the GPU once (occupancy-derived)
+  int U;          // items per thread per trip
+  bool pred;      // predicated
+  bool chunk;     // chunked access
+  int* launches;  // incremented per kernel launch
+  // optional per-kernel timing: called right before and right after a launch
+  void (*mark)(void* timer, cudaStream_t s);
+  void* timer;
+};
+
+inline void kmark(const LaunchCfg& c) {
+  if (c.mark) c.mark(c.timer, c.stream);
+}
+
+// Ungrouped AGGREGATE buffers: raw accumulators (zero between runs) and the
+// decoded result row.
+struct AggOut {
+  unsigned long long* acc;  // [n_aggs + 1], last = hidden row count
+  int64_t* result;          // [n_aggs]
+  unsigned int* done;       // block ticket (zero between runs)
+};
+
+// PROJECT buffers.
+struct ProjOut {
+  void* col[PV_MAX_PROJ];       // typed output columns
+  int64_t capacity;             // rows
+  unsigned long long* cursor;   // single pass: write cursor (zero between runs)
+  int64_t* count;               // rows written (min(total, capacity))
+  unsigned int* done;           // single pass: block ticket
+  int64_t* tile_count;          // multi pass: matches per tile
+  int64_t* tile_offset;         // multi pass: exclusive prefix of tile_count
+  int64_t n_tiles;
+};
+
+// Grouped aggregation description shared by the group kernels and the host.
+struct GroupDesc {
+  int n_keys;
+  int n_aggs;
+  int32_t func[PV_MAX_AGGS];
+  int key64[PV_MAX_KEYS];        // key part is a 64-bit source (1 part only)
+  int64_t key_min[PV_MAX_KEYS];  // perfect array: domain of each part
+  int64_t key_span[PV_MAX_KEYS];
+};
+
+// Grouped aggregation table + extraction buffers (owned by a result).
+struct GroupOut {
+  // Global table.  Slot s: keys[s] (EMPTY = ~0; perfect: unused) and
+  // vals[s * stride + a] for a < n_aggs, vals[s * stride + n_aggs] = row count.
+  unsigned long long* keys;
+  unsigned long long* vals;
+  int64_t cap;        // slots (power of two for hashed tables; domain for perfect)
+  int log2cap;
+  int stride;         // words per slot in vals
+  int ht;             // pv_ht_kind
+  int hash;           // pv_hash_fn
+  int cuckoo_k;
+  int max_evictions;
+  uint64_t seed[4];
+  int local_slots;    // LOCAL strategy: slots of the per-CTA shared-memory table
+  // Extraction (dense result columns, int64): out[c * out_cap + row].
+  int64_t* out;
+  int64_t out_cap;
+  unsigned long long* out_count;
+};
+
+struct ShapeEntry {
+  std::string sig;
+  int mode;
+  // Launchers return PV_OK or PV_ERR_UNSUPPORTED (no instantiation for the variant).
+  pv_status (*aggregate)(const LaunchCfg&, const KParams&, const AggOut&);
+  pv_status (*project)(const LaunchCfg&, const KParams&, const ProjOut&, int exec);
+  pv_status (*grouped)(const LaunchCfg&, const KParams&, const GroupDesc&, const GroupOut&,
+                       const pv_variant&);
+};
+
+void register_shape(const ShapeEntry& e);
+const ShapeEntry* find_shape(const std::string& sig);
+void register_scan_shapes();
+void register_group_shapes();
+
+// Grid size: grid_mult * SMs, or the number of CTAs resident at once; never
+// more CTAs than there is work for (items_per_cta items each).
+int grid_for(const LaunchCfg& c, const void* kernel, size_t smem, int64_t work_items,
+             int64_t items_per_cta);
+
+}  // namespace pv

@@ -1,0 +1,365 @@
+"""Python binding of libpv (argument marshalling only).
+
+The functions ``pv_*`` mirror the C ABI of include/pv.h one to one through
+ctypes.  :class:`Context` is a thin convenience layer: it registers torch
+CUDA tensors as columns, translates a neutral plan dict (the pipeline
+programs of a query, Table 2; format in ``oracle`` and ``workloads``) into
+pv_build_spec / pv_pipeline_spec structs, and copies results back.  Every
+step of a pipeline runs in libpv's CUDA kernels; there is no CPU path here.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpv.so")
+
+# ---- constants (include/pv.h) ----------------------------------------------
+PV_OK = 0
+STATUS = {0: "PV_OK", -1: "PV_ERR_INVALID_ARG", -2: "PV_ERR_UNSUPPORTED", -3: "PV_ERR_HT_FULL",
+          -4: "PV_ERR_CUCKOO_CYCLE", -5: "PV_ERR_KEY_OUT_OF_RANGE", -6: "PV_ERR_DUP_BUILD_KEY",
+          -7: "PV_ERR_OUTPUT_OVERFLOW", -8: "PV_ERR_TIMEOUT", -9: "PV_ERR_CUDA", -10: "PV_ERR_OOM"}
+PV_I32, PV_I64, PV_U8 = 0, 1, 2
+MAX_PREDS, MAX_PROBES, MAX_KEYS, MAX_AGGS, MAX_TERMS, MAX_PROJ, MAX_PAYLOAD = 4, 4, 2, 8, 3, 4, 1
+OPS = {"lt": 0, "le": 1, "gt": 2, "ge": 3, "eq": 4, "between": 5}
+FUNCS = {"sum": 0, "count": 1, "min": 2, "max": 3}
+TERMS = {"x": 0, "x_plus_c": 1, "c_minus_x": 2}
+REF_COL, REF_PAYLOAD = 0, 1
+HT = {"linear": 0, "cuckoo": 1, "perfect": 2}
+HASH = {"murmur": 0, "multshift": 1}
+EXEC = {"single": 0, "multi": 1}
+AGG = {"local": 0, "global": 1}
+PRED = {"branch": 0, "predicated": 1}
+ACCESS = {"grid": 0, "chunked": 1}
+_NP_OF = {PV_I32: np.int32, PV_I64: np.int64, PV_U8: np.uint8}
+
+
+class pv_ref(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("a", ctypes.c_int32), ("b", ctypes.c_int32)]
+
+
+class pv_pred(ctypes.Structure):
+    _fields_ = [("col", ctypes.c_int32), ("op", ctypes.c_int32), ("c0", ctypes.c_int64), ("c1", ctypes.c_int64)]
+
+
+class pv_term(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("x", pv_ref), ("c", ctypes.c_int64)]
+
+
+class pv_agg(ctypes.Structure):
+    _fields_ = [("func", ctypes.c_int32), ("n_terms", ctypes.c_int32), ("terms", pv_term * MAX_TERMS)]
+
+
+class pv_probe(ctypes.Structure):
+    _fields_ = [("ht", ctypes.c_int32), ("fk", ctypes.c_int32)]
+
+
+class pv_build_spec(ctypes.Structure):
+    _fields_ = [("key", ctypes.c_int32), ("n_preds", ctypes.c_int32), ("preds", pv_pred * MAX_PREDS),
+                ("n_payload", ctypes.c_int32), ("payload", ctypes.c_int32 * MAX_PAYLOAD)]
+
+
+class pv_ht_variant(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("hash", ctypes.c_int32), ("cuckoo_k", ctypes.c_int32),
+                ("max_evictions", ctypes.c_int32), ("load_factor", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class pv_pipeline_spec(ctypes.Structure):
+    _fields_ = [("n_preds", ctypes.c_int32), ("preds", pv_pred * MAX_PREDS),
+                ("n_probes", ctypes.c_int32), ("probes", pv_probe * MAX_PROBES),
+                ("n_keys", ctypes.c_int32), ("keys", pv_ref * MAX_KEYS),
+                ("n_aggs", ctypes.c_int32), ("aggs", pv_agg * MAX_AGGS),
+                ("n_proj", ctypes.c_int32), ("proj", pv_ref * MAX_PROJ),
+                ("capacity_hint", ctypes.c_int64)]
+
+
+class pv_variant(ctypes.Structure):
+    _fields_ = [("exec", ctypes.c_int32), ("agg", ctypes.c_int32), ("pred", ctypes.c_int32),
+                ("access", ctypes.c_int32), ("ht", ctypes.c_int32), ("hash", ctypes.c_int32),
+                ("block", ctypes.c_int32), ("grid_mult", ctypes.c_int32),
+                ("items_per_thread", ctypes.c_int32), ("threads_per_table", ctypes.c_int32),
+                ("cuckoo_k", ctypes.c_int32), ("reserved", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+_P = ctypes.POINTER
+_SIGS = {
+    "pv_create": (ctypes.c_int32, [_P(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p, ALLOC_FN, FREE_FN, ctypes.c_void_p]),
+    "pv_destroy": (ctypes.c_int32, [ctypes.c_void_p]),
+    "pv_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "pv_device_info": (ctypes.c_int32, [ctypes.c_void_p, _P(ctypes.c_int32), _P(ctypes.c_int64)]),
+    "pv_register_column": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int32,
+                                            ctypes.c_void_p, ctypes.c_int64, _P(ctypes.c_int32)]),
+    "pv_column_stats": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, _P(ctypes.c_int64), _P(ctypes.c_int64)]),
+    "pv_build_hash_table": (ctypes.c_int32, [ctypes.c_void_p, _P(pv_build_spec), _P(pv_ht_variant), _P(ctypes.c_int32)]),
+    "pv_run_pipeline": (ctypes.c_int32, [ctypes.c_void_p, _P(pv_pipeline_spec), _P(pv_variant), _P(ctypes.c_int32)]),
+    "pv_rerun": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
+    "pv_sync": (ctypes.c_int32, [ctypes.c_void_p]),
+    "pv_set_timeout_ms": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int64]),
+    "pv_result_shape": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, _P(ctypes.c_int64), _P(ctypes.c_int32)]),
+    "pv_result_col_type": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_int32)]),
+    "pv_fetch_result": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                         ctypes.c_int64, ctypes.c_int32]),
+    "pv_free": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
+    "pv_graph_capture_begin": (ctypes.c_int32, [ctypes.c_void_p]),
+    "pv_graph_capture_end": (ctypes.c_int32, [ctypes.c_void_p, _P(ctypes.c_int32)]),
+    "pv_graph_launch": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
+    "pv_l2_flush": (ctypes.c_int32, [ctypes.c_void_p]),
+    "pv_last_launch_count": (ctypes.c_int32, [ctypes.c_void_p, _P(ctypes.c_int32)]),
+    "pv_set_kernel_timing": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
+    "pv_kernel_times": (ctypes.c_int32, [ctypes.c_void_p, _P(ctypes.c_float), ctypes.c_int32, _P(ctypes.c_int32)]),
+    "pv_debug_spin": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int64]),
+}
+EXPORTS = tuple(_SIGS)
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads libpv.so.  Raises if it has not been built: there is no fallback."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing; build it with paper_1709_00700_gb300.build.build()")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def __getattr__(name):  # pv_create, pv_run_pipeline, ... resolve to the C functions
+    if name.startswith("pv_") and name in _SIGS:
+        return getattr(load(), name)
+    raise AttributeError(name)
+
+
+class PVError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def variant(exec="single", agg="local", pred="branch", access="grid", ht="linear", hash="murmur",
+            block=256, grid_mult=0, items_per_thread=2, threads_per_table=0, cuckoo_k=3, seed=0) -> pv_variant:
+    """A pv_variant from readable names (the variant dimensions of Section 3.3)."""
+    return pv_variant(EXEC[exec], AGG[agg], PRED[pred], ACCESS[access], HT[ht], HASH[hash], block, grid_mult,
+                      items_per_thread, threads_per_table, cuckoo_k, 0, seed)
+
+
+def ht_variant(kind="linear", hash="murmur", cuckoo_k=3, max_evictions=0, load_factor=0.5, seed=0) -> pv_ht_variant:
+    return pv_ht_variant(HT[kind], HASH[hash], cuckoo_k, max_evictions, load_factor, seed)
+
+
+_TORCH_TYPE = None
+
+
+def _type_of(t) -> int:
+    import torch
+    m = {torch.int32: PV_I32, torch.int64: PV_I64, torch.uint8: PV_U8}
+    if t.dtype not in m:
+        raise TypeError(f"unsupported column dtype {t.dtype}")
+    return m[t.dtype]
+
+
+class Context:
+    """One pv_ctx on a dedicated CUDA stream, allocating through torch."""
+
+    def __init__(self, device: int = 0, use_torch_allocator: bool = True):
+        import torch
+        self.torch = torch
+        self.lib = load()
+        self.device = device
+        self.stream = torch.cuda.Stream(device=device)
+        self._alloc_cb = self._free_cb = None
+        if use_torch_allocator:
+            dev, st = device, self.stream
+
+            def _alloc(nbytes, _user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev, st)
+                except Exception:  # noqa: BLE001 - reported to C as NULL (PV_ERR_OOM)
+                    return None
+
+            def _free(ptr, _user):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._alloc_cb, self._free_cb = ALLOC_FN(_alloc), FREE_FN(_free)
+        h = ctypes.c_void_p()
+        self._check(self.lib.pv_create(ctypes.byref(h), device, ctypes.c_void_p(self.stream.cuda_stream),
+                                       self._alloc_cb, self._free_cb, None), ctx=None)
+        self.h = h
+        self.cols = {}      # (table, col) -> handle
+        self.keep = {}      # (table, col) -> tensor (borrowed by libpv)
+        self.tables = {}    # build key -> ht handle
+
+    # -- plumbing -------------------------------------------------------------
+    def _check(self, st: int, ctx="self"):
+        if st != PV_OK:
+            msg = "" if ctx is None else self.lib.pv_last_error(self.h).decode()
+            raise PVError(st, msg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pv_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def sync(self):
+        self._check(self.lib.pv_sync(self.h))
+
+    def device_info(self):
+        sm, l2 = ctypes.c_int32(), ctypes.c_int64()
+        self._check(self.lib.pv_device_info(self.h, ctypes.byref(sm), ctypes.byref(l2)))
+        return sm.value, l2.value
+
+    def last_launch_count(self) -> int:
+        n = ctypes.c_int32()
+        self._check(self.lib.pv_last_launch_count(self.h, ctypes.byref(n)))
+        return n.value
+
+    def set_kernel_timing(self, on: bool):
+        self._check(self.lib.pv_set_kernel_timing(self.h, 1 if on else 0))
+
+    def kernel_times(self) -> list:
+        buf = (ctypes.c_float * 64)()
+        n = ctypes.c_int32()
+        self._check(self.lib.pv_kernel_times(self.h, buf, 64, ctypes.byref(n)))
+        return [buf[i] for i in range(min(n.value, 64))]
+
+    # -- columns ----------------------------------------------------------------
+    def register_table(self, table: str, cols: dict):
+        """Registers device tensors (1-D, contiguous) as borrowed columns."""
+        torch = self.torch
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        for name, t in cols.items():
+            if not isinstance(t, torch.Tensor):
+                t = torch.from_numpy(np.ascontiguousarray(t)).to(f"cuda:{self.device}")
+            assert t.is_cuda and t.is_contiguous() and t.dim() == 1
+            h = ctypes.c_int32()
+            self._check(self.lib.pv_register_column(self.h, table.encode(), name.encode(), _type_of(t),
+                                                    ctypes.c_void_p(t.data_ptr()), t.numel(), ctypes.byref(h)))
+            self.cols[(table, name)] = h.value
+            self.keep[(table, name)] = t
+        return self
+
+    def column_stats(self, table: str, name: str):
+        lo, hi = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.lib.pv_column_stats(self.h, self.cols[(table, name)], ctypes.byref(lo), ctypes.byref(hi)))
+        return lo.value, hi.value
+
+    # -- builds -----------------------------------------------------------------
+    def _pred(self, table, p) -> pv_pred:
+        c1 = int(p[3]) if p[1] == "between" else 0
+        return pv_pred(self.cols[(table, p[0])], OPS[p[1]], int(p[2]), c1)
+
+    def build(self, b: dict, htv: pv_ht_variant) -> int:
+        spec = pv_build_spec()
+        spec.key = self.cols[(b["table"], b["key"])]
+        fl = b.get("filters", [])
+        spec.n_preds = len(fl)
+        for i, p in enumerate(fl):
+            spec.preds[i] = self._pred(b["table"], p)
+        pay = b.get("payload", [])
+        spec.n_payload = len(pay)
+        for i, c in enumerate(pay):
+            spec.payload[i] = self.cols[(b["table"], c)]
+        h = ctypes.c_int32()
+        self._check(self.lib.pv_build_hash_table(self.h, ctypes.byref(spec), ctypes.byref(htv), ctypes.byref(h)))
+        return h.value
+
+    # -- pipelines --------------------------------------------------------------
+    def spec(self, plan: dict, ht_handles=()) -> pv_pipeline_spec:
+        fact = plan["fact"]
+        s = pv_pipeline_spec()
+
+        def ref(r) -> pv_ref:
+            if isinstance(r, str):
+                return pv_ref(REF_COL, self.cols[(fact, r)], 0)
+            kind, p, i = r
+            assert kind == "payload"
+            return pv_ref(REF_PAYLOAD, int(p), int(i))
+
+        fl = plan.get("filters", [])
+        s.n_preds = len(fl)
+        for i, p in enumerate(fl):
+            s.preds[i] = self._pred(fact, p)
+        pr = plan.get("probes", [])
+        s.n_probes = len(pr)
+        for i, q in enumerate(pr):
+            s.probes[i] = pv_probe(ht_handles[q["build"]], self.cols[(fact, q["fk"])])
+        keys = plan.get("group_by", [])
+        s.n_keys = len(keys)
+        for i, r in enumerate(keys):
+            s.keys[i] = ref(r)
+        aggs = plan.get("aggs", [])
+        s.n_aggs = len(aggs)
+        for i, a in enumerate(aggs):
+            terms = a[1] if len(a) > 1 else []
+            s.aggs[i].func = FUNCS[a[0]]
+            s.aggs[i].n_terms = len(terms)
+            for j, t in enumerate(terms):
+                c = int(t[2]) if t[0] != "x" else 0
+                s.aggs[i].terms[j] = pv_term(TERMS[t[0]], ref(t[1]), c)
+        proj = plan.get("project", [])
+        s.n_proj = len(proj)
+        for i, r in enumerate(proj):
+            s.proj[i] = ref(r)
+        s.capacity_hint = int(plan.get("capacity_hint", 0))
+        return s
+
+    def build_all(self, plan: dict, htv: pv_ht_variant) -> list:
+        return [self.build(b, htv) for b in plan.get("builds", [])]
+
+    def run(self, plan: dict, var: pv_variant, ht_handles=()) -> int:
+        s = self.spec(plan, ht_handles)
+        h = ctypes.c_int32()
+        self._check(self.lib.pv_run_pipeline(self.h, ctypes.byref(s), ctypes.byref(var), ctypes.byref(h)))
+        return h.value
+
+    def rerun(self, res: int):
+        self._check(self.lib.pv_rerun(self.h, res))
+
+    def fetch(self, res: int) -> list:
+        """Result columns as numpy arrays of their result type."""
+        n, m = ctypes.c_int64(), ctypes.c_int32()
+        self._check(self.lib.pv_result_shape(self.h, res, ctypes.byref(n), ctypes.byref(m)))
+        out = []
+        for c in range(m.value):
+            t = ctypes.c_int32()
+            self._check(self.lib.pv_result_col_type(self.h, res, c, ctypes.byref(t)))
+            a = np.empty(max(n.value, 1), dtype=_NP_OF[t.value])
+            self._check(self.lib.pv_fetch_result(self.h, res, c, ctypes.c_void_p(a.ctypes.data), len(a), 0))
+            out.append(a[: n.value])
+        return out
+
+    def free(self, handle: int):
+        self._check(self.lib.pv_free(self.h, handle))
+
+    def query(self, plan: dict, var: pv_variant, htv: pv_ht_variant | None = None, keep: bool = False):
+        """Builds, runs and fetches a whole plan; returns int64 result columns
+        (grouped results sorted by key, projections as produced)."""
+        hts = self.build_all(plan, htv or ht_variant())
+        res = self.run(plan, var, hts)
+        cols = [c.astype(np.int64) for c in self.fetch(res)]
+        if not keep:
+            self.free(res)
+            for h in hts:
+                self.free(h)
+        nk = len(plan.get("group_by", []))
+        if nk and cols and len(cols[0]):
+            order = np.lexsort(tuple(cols[i] for i in reversed(range(nk))))
+            cols = [c[order] for c in cols]
+        return cols

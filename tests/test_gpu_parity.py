@@ -1,0 +1,358 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Every result is int64 fixed point, so the bar is bit-exact equality.
+Grouped results are compared after sorting by key (group order is not
+defined); single-pass projections after sorting rows (write order is not
+defined); multi-pass projections in input order exactly.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+from paper_1709_00700_gb300 import datagen, pv, workloads
+from tests.gpu_util import assert_same, register, want
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    assert torch.cuda.is_available()
+    c = pv.Context(0)
+    yield c
+    c.close()
+
+
+def run_or_skip(ctx, plan, var, htv=None):
+    try:
+        return ctx.query(plan, var, htv)
+    except pv.PVError as e:
+        if e.status == -2:  # no instantiation for this variant (e.g. registers for 1024 threads)
+            return None
+        raise
+
+
+SCAN_VARIANTS = [dict(pred=p, access=a, items_per_thread=u, block=b, grid_mult=g)
+                 for p, a, u, b, g in itertools.product(["branch", "predicated"], ["grid", "chunked"],
+                                                        [1, 2, 4], [64, 256, 1024], [0, 1])]
+
+
+# ---------------------------------------------------------------- AGGREGATE
+@pytest.mark.parametrize("n", [0, 1, 3, 5, 4096, 100_003])
+def test_filter_aggregate_all_variants(ctx, n):
+    t = {"t": datagen.table_filter_agg(n, seed=n + 1)}
+    register(ctx, t)
+    plan = workloads.filter_agg_plan()
+    w = want(plan, t)
+    ran = 0
+    for kw in SCAN_VARIANTS:
+        got = run_or_skip(ctx, plan, pv.variant(**kw))
+        if got is None:
+            continue
+        ran += 1
+        assert_same(got, w, ctxmsg=str(kw))
+    assert ran >= len(SCAN_VARIANTS) // 2
+
+
+def test_filter_aggregate_lattice_closed_form(ctx):
+    m = 3
+    t = {"t": datagen.table_lattice(m)}
+    register(ctx, t)
+    got = ctx.query(workloads.filter_agg_plan(), pv.variant())
+    count = 210 * m
+    total = (100 * count + 10_000 * (m * (m - 1) // 2) * 210 + 100 * sum(range(20, 41)) * 10 * m
+             + sum(range(10)) * 21 * m)
+    assert [int(got[0][0]), int(got[1][0])] == [total, count]
+
+
+@pytest.mark.parametrize("a_lt,b_lo,b_hi", [(0, 20, 40), (100, 0, 99), (10, 40, 20), (-5, 0, 10)])
+def test_filter_aggregate_degenerate_predicates(ctx, a_lt, b_lo, b_hi):
+    t = {"t": datagen.table_filter_agg(20_000, seed=4)}
+    register(ctx, t)
+    plan = workloads.filter_agg_plan(a_lt, b_lo, b_hi)
+    for pred in ("branch", "predicated"):
+        assert_same(ctx.query(plan, pv.variant(pred=pred)), want(plan, t), ctxmsg=pred)
+
+
+def test_lowcard_totals_and_minmax(ctx):
+    li = {"li": datagen.table_lowcard_groups(77_777, seed=9)}
+    register(ctx, li)
+    plan = dict(workloads.lowcard_plan(), group_by=[])
+    w = want(plan, li)
+    for pred in ("branch", "predicated"):
+        assert_same(ctx.query(plan, pv.variant(pred=pred)), w, ctxmsg=pred)
+    kv = {"kv": datagen.table_keyval(33_333, 10, seed=3)}
+    register(ctx, kv)
+    plan = {"fact": "kv", "filters": [["val", "between", 1000, 900_000]],
+            "aggs": [["sum", [["x", "val"]]], ["count"], ["min", [["x", "val"]]], ["max", [["x", "val"]]]]}
+    for pred in ("branch", "predicated"):
+        assert_same(ctx.query(plan, pv.variant(pred=pred)), want(plan, kv), ctxmsg=pred)
+    # MIN/MAX over no row read 0, as the oracle reports
+    plan["filters"] = [["val", "lt", -1]]
+    assert [int(c[0]) for c in ctx.query(plan, pv.variant())] == [0, 0, 0, 0]
+
+
+# ---------------------------------------------------------------- PROJECT
+@pytest.mark.parametrize("n", [0, 2, 7, 4097, 250_001])
+def test_filter_project_single_and_multi_pass(ctx, n):
+    t = {"t": datagen.table_filter_agg(n, seed=n + 2)}
+    register(ctx, t)
+    plan = workloads.filter_project_plan()
+    w = want(plan, t)
+    for kw in SCAN_VARIANTS[::3]:
+        for ex in ("single", "multi"):
+            got = run_or_skip(ctx, plan, pv.variant(exec=ex, **kw))
+            if got is None:
+                continue
+            assert got[0].dtype == np.int32 and got[1].dtype == np.int64
+            assert_same(got, w, ordered=(ex == "multi"), ctxmsg=f"{ex} {kw}")
+
+
+def test_project_golden_example(ctx):
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "select_b_where_a_lt_5.json")))
+    tables = {t: {c: np.array(v["values"], dtype=v["dtype"]) for c, v in cols.items()} for t, cols in g["tables"].items()}
+    # the compiled projection shape reads (a, b, price); pad the table with a price column
+    tables["t"]["price"] = np.arange(8, dtype=np.int64)
+    register(ctx, tables)
+    plan = {"fact": "t", "filters": [["a", "lt", 5]], "project": ["b", "price"]}
+    got = ctx.query(plan, pv.variant(exec="multi"))
+    assert list(map(int, got[0])) == g["expected"]["cols"][0]
+
+
+@pytest.mark.parametrize("ex", ["single", "multi"])
+def test_project_output_overflow_is_reported(ctx, ex):
+    t = {"t": datagen.table_filter_agg(50_000, seed=5)}
+    register(ctx, t)
+    plan = dict(workloads.filter_project_plan(), capacity_hint=10)
+    with pytest.raises(pv.PVError) as e:
+        ctx.query(plan, pv.variant(exec=ex))
+    assert e.value.status == -7
+    ctx.sync()  # the error word was cleared by the failing fetch
+
+
+# ---------------------------------------------------------------- HASH_AGGREGATE
+GROUP_VARIANTS = [dict(agg=a, ht=h, exec=e, pred=p, access=ac, items_per_thread=u, threads_per_table=tp, hash=hs)
+                  for a, h, e, p, ac, u, tp, hs in itertools.product(
+                      ["local", "global"], ["linear", "cuckoo", "perfect"], ["single", "multi"],
+                      ["branch", "predicated"], ["grid", "chunked"], [1, 2], [0, 1], ["murmur", "multshift"])]
+
+
+def _grouped_all_variants(ctx, plan, tables, step=1, min_ran=10):
+    w = want(plan, tables)
+    ran = 0
+    for kw in GROUP_VARIANTS[::step]:
+        got = run_or_skip(ctx, plan, pv.variant(**kw))
+        if got is None:
+            continue
+        ran += 1
+        assert_same(got, w, ctxmsg=str(kw))
+    assert ran >= min_ran
+    return ran
+
+
+def test_lowcard_grouped_all_variants(ctx):
+    li = {"li": datagen.table_lowcard_groups(60_001, seed=11)}
+    register(ctx, li)
+    _grouped_all_variants(ctx, workloads.lowcard_plan(), li, min_ran=60)
+
+
+@pytest.mark.parametrize("g,dist", [(1, "uniform"), (10, "zipf"), (1000, "uniform"), (1000, "zipf"),
+                                    (50_000, "uniform")])
+def test_keyval_grouped_all_variants(ctx, g, dist):
+    kv = {"kv": datagen.table_keyval(120_007, g, dist, seed=g)}
+    register(ctx, kv)
+    _grouped_all_variants(ctx, workloads.keyval_plan(), kv, step=3, min_ran=20)
+    _grouped_all_variants(ctx, workloads.keyval_plan(val_lt=300_000), kv, step=7, min_ran=8)
+
+
+def test_keyval_negative_and_extreme_keys(ctx):
+    rng = np.random.default_rng(5)
+    key = rng.choice(np.array([-1, -2, 0, 2**31 - 1, -2**31, 7], np.int32), 10_000)
+    kv = {"kv": {"key": key, "val": rng.integers(-10**9, 10**9, 10_000).astype(np.int64)}}
+    register(ctx, kv)
+    w = want(workloads.keyval_plan(), kv)
+    for kw in GROUP_VARIANTS[::5]:
+        if kw["ht"] == "perfect":
+            continue  # the key domain spans 2^32 values
+        got = run_or_skip(ctx, workloads.keyval_plan(), pv.variant(**kw))
+        if got is not None:
+            assert_same(got, w, ctxmsg=str(kw))
+
+
+def test_grouped_rerun_is_clean(ctx):
+    kv = {"kv": datagen.table_keyval(100_000, 5000, seed=2)}
+    register(ctx, kv)
+    plan = workloads.keyval_plan()
+    w = want(plan, kv)
+    for kw in (dict(ht="linear"), dict(ht="cuckoo", exec="multi"), dict(ht="perfect", agg="global")):
+        res = ctx.run(plan, pv.variant(**kw))
+        for _ in range(3):
+            ctx.rerun(res)
+        cols = [c.astype(np.int64) for c in ctx.fetch(res)]
+        order = np.argsort(cols[0], kind="stable")
+        assert_same([c[order] for c in cols], w, ctxmsg=str(kw))
+        ctx.free(res)
+
+
+def test_grouped_table_full_is_reported(ctx):
+    kv = {"kv": datagen.table_keyval(50_000, 1000, seed=6)}
+    register(ctx, kv)
+    plan = dict(workloads.keyval_plan(), capacity_hint=1)
+    with pytest.raises(pv.PVError) as e:
+        ctx.query(plan, pv.variant(ht="linear", agg="global"))
+    assert e.value.status == -3
+
+
+# ---------------------------------------------------------------- joins
+def _star_small(n, seed, lim=None):
+    s = datagen.star_schema(n, seed)
+    return {"fact": s["fact"], **{d: s[d] for d, _, _ in datagen.STAR_DIMS}}
+
+
+@pytest.mark.parametrize("build_kind", ["linear", "cuckoo", "perfect"])
+@pytest.mark.parametrize("hash_fn", ["murmur", "multshift"])
+def test_star_join_all_build_kinds(ctx, build_kind, hash_fn):
+    s = _star_small(200_003, seed=31)
+    register(ctx, s)
+    plan = workloads.star_plan({"d_a": 60, "d_b": 50, "d_c": 30, "d_d": 40})
+    w = want(plan, s)
+    htv = pv.ht_variant(build_kind, hash_fn)
+    ran = 0
+    for kw in GROUP_VARIANTS[::6]:
+        try:
+            got = ctx.query(plan, pv.variant(**kw), htv)
+        except pv.PVError as e:
+            if e.status == -2:
+                continue
+            raise
+        ran += 1
+        assert_same(got, w, ctxmsg=f"{build_kind} {kw}")
+    assert ran >= 8
+
+
+def test_star_join_negative_one_keys_and_payloads(ctx):
+    # build key -1 and payloads (-1, -1) exercise both side slots
+    d = {}
+    for name, rows, g in datagen.STAR_DIMS:
+        d[name] = {"key": np.arange(-1, 9, dtype=np.int32), "f": np.zeros(10, np.int32),
+                   "g": np.full(10, -1, np.int32)}
+        d[name]["g"][5:] = 3
+    rng = np.random.default_rng(3)
+    fact = {f"fk_{n[2:]}": rng.integers(-2, 10, 20_000).astype(np.int32) for n, _, _ in datagen.STAR_DIMS}
+    fact["revenue"] = rng.integers(100, 10**7, 20_000).astype(np.int64)
+    tables = {"fact": fact, **d}
+    register(ctx, tables)
+    plan = workloads.star_plan({k: 100 for k in ("d_a", "d_b", "d_c", "d_d")})
+    w = want(plan, tables)
+    for kind in ("linear", "cuckoo", "perfect"):
+        for kw in (dict(ht="linear"), dict(ht="cuckoo", exec="multi"), dict(ht="perfect"),
+                   dict(ht="perfect", agg="global", pred="predicated")):
+            assert_same(ctx.query(plan, pv.variant(**kw), pv.ht_variant(kind)), w, ctxmsg=f"{kind} {kw}")
+
+
+@pytest.mark.parametrize("fixture", ["table2_join_group_x.json", "table2_join_group_y.json"])
+def test_table2_golden_on_gpu(ctx, fixture):
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", fixture)))
+    tables = {t: {c: np.array(v["values"], dtype=v["dtype"]) for c, v in cols.items()} for t, cols in g["tables"].items()}
+    register(ctx, tables)
+    for kind in ("linear", "cuckoo", "perfect"):
+        for kw in (dict(), dict(pred="predicated"), dict(agg="global", ht="perfect")):
+            got = ctx.query(g["plan"], pv.variant(items_per_thread=1, **kw), pv.ht_variant(kind))
+            assert [list(map(int, c)) for c in got] == g["expected"]["cols"]
+
+
+@pytest.mark.parametrize("kind", ["linear", "cuckoo", "perfect"])
+def test_duplicate_build_key_is_reported(ctx, kind):
+    dim = {"key": np.array([1, 2, 3, 2], np.int32)}
+    fact = {"fk": np.array([1, 2, 3], np.int32)}
+    register(ctx, {"dimdup": dim, "factdup": fact})
+    plan = {"fact": "factdup", "builds": [{"table": "dimdup", "key": "key", "payload": []}],
+            "probes": [{"build": 0, "fk": "fk"}], "aggs": [["count"]]}
+    with pytest.raises(pv.PVError) as e:
+        ctx.query(plan, pv.variant(), pv.ht_variant(kind))
+    assert e.value.status == -6
+
+
+def test_join_lattice_count(ctx):
+    D, r, thr = 1234, 3, 37
+    dim = {"key": np.arange(D, dtype=np.int32), "f": (np.arange(D) % 100).astype(np.int32)}
+    fact = {"fk": (np.arange(D * r) % D).astype(np.int32)}
+    register(ctx, {"jdim": dim, "jfact": fact})
+    plan = {"fact": "jfact", "builds": [{"table": "jdim", "key": "key", "filters": [["f", "lt", thr]], "payload": []}],
+            "probes": [{"build": 0, "fk": "fk"}], "aggs": [["count"]]}
+    for kind in ("linear", "cuckoo", "perfect"):
+        got = ctx.query(plan, pv.variant(), pv.ht_variant(kind))
+        assert int(got[0][0]) == r * ((D // 100) * thr + min(D % 100, thr))
+
+
+# ---------------------------------------------------------------- runtime
+def test_unsupported_shape_is_reported(ctx):
+    t = {"t": datagen.table_filter_agg(1000, seed=1)}
+    register(ctx, t)
+    plan = {"fact": "t", "filters": [["a", "lt", 3]], "aggs": [["max", [["x", "b"]]]]}
+    with pytest.raises(pv.PVError) as e:
+        ctx.query(plan, pv.variant())
+    assert e.value.status == -2
+
+
+def test_misaligned_column_is_rejected(ctx):
+    import ctypes
+    import torch
+    x = torch.zeros(64, dtype=torch.int32, device="cuda")
+    h = ctypes.c_int32()
+    st = ctx.lib.pv_register_column(ctx.h, b"t", b"x", 0, ctypes.c_void_p(x.data_ptr() + 4), 10, ctypes.byref(h))
+    assert st == -1
+
+
+def test_watchdog_timeout_then_recovers(ctx):
+    lib = ctx.lib
+    assert lib.pv_set_timeout_ms(ctx.h, 100) == 0
+    assert lib.pv_debug_spin(ctx.h, 1_000_000_000) == 0  # one second of bounded spinning
+    assert lib.pv_sync(ctx.h) == -8
+    assert lib.pv_set_timeout_ms(ctx.h, 60_000) == 0
+    assert lib.pv_sync(ctx.h) == 0
+
+
+def test_graph_replay_of_reruns(ctx):
+    import ctypes
+    t = {"t": datagen.table_filter_agg(300_000, seed=12)}
+    kv = {"kv": datagen.table_keyval(300_000, 777, seed=13)}
+    register(ctx, t)
+    register(ctx, kv)
+    p1, p2 = workloads.filter_agg_plan(), workloads.keyval_plan()
+    r1 = ctx.run(p1, pv.variant())
+    r2 = ctx.run(p2, pv.variant(ht="perfect"))
+    ctx.sync()
+    lib = ctx.lib
+    assert lib.pv_l2_flush(ctx.h) == 0
+    assert lib.pv_graph_capture_begin(ctx.h) == 0
+    for _ in range(4):
+        assert lib.pv_l2_flush(ctx.h) == 0
+        assert lib.pv_rerun(ctx.h, r1) == 0
+        assert lib.pv_rerun(ctx.h, r2) == 0
+    g = ctypes.c_int32()
+    assert lib.pv_graph_capture_end(ctx.h, ctypes.byref(g)) == 0
+    for _ in range(3):
+        assert lib.pv_graph_launch(ctx.h, g.value) == 0
+    ctx.sync()
+    assert_same([c.astype(np.int64) for c in ctx.fetch(r1)], want(p1, t))
+    got = [c.astype(np.int64) for c in ctx.fetch(r2)]
+    order = np.argsort(got[0])
+    assert_same([c[order] for c in got], want(p2, kv))
+    ctx.free(g.value)
+    ctx.free(r1)
+    ctx.free(r2)
+
+
+def test_cuda_malloc_async_allocator():
+    c = pv.Context(0, use_torch_allocator=False)
+    t = {"t": datagen.table_filter_agg(10_000, seed=3)}
+    register(c, t)
+    assert_same(c.query(workloads.filter_agg_plan(), pv.variant()), want(workloads.filter_agg_plan(), t))
+    c.close()
