@@ -614,6 +614,10 @@ static pv_status alloc_result(pv_ctx* c, Result& r) {
   g.out = static_cast<int64_t*>(grab(static_cast<size_t>(g.out_cap) * ncol * 8));
   g.out_count = static_cast<unsigned long long*>(grab(16));
   if (!g.keys || !g.vals || !g.out || !g.out_count) return fail(c, PV_ERR_OOM, "allocator returned NULL");
+  // Empty table once at allocation; extraction empties every slot it reads.
+  PV_CUDA(c, cudaMemsetAsync(g.keys, 0xFF, static_cast<size_t>(slots) * 8, c->stream));
+  PV_CUDA(c, cudaMemsetAsync(g.vals, 0, static_cast<size_t>(slots) * g.stride * 8, c->stream));
+  PV_CUDA(c, cudaMemsetAsync(g.out_count, 0, 16, c->stream));
   r.n_cols = ncol;
   for (int i = 0; i < ncol; ++i) r.col_type[i] = PV_I64;
   return PV_OK;

@@ -178,7 +178,7 @@ class Context:
         self.lib = load()
         self.device = device
         self.stream = torch.cuda.Stream(device=device)
-        self._alloc_cb = self._free_cb = None
+        self._alloc_cb, self._free_cb = ALLOC_FN(), FREE_FN()  # NULL: libpv uses cudaMallocAsync
         if use_torch_allocator:
             dev, st = device, self.stream
 

@@ -106,8 +106,12 @@ def test_filter_project_single_and_multi_pass(ctx, n):
             got = run_or_skip(ctx, plan, pv.variant(exec=ex, **kw))
             if got is None:
                 continue
-            assert got[0].dtype == np.int32 and got[1].dtype == np.int64
             assert_same(got, w, ordered=(ex == "multi"), ctxmsg=f"{ex} {kw}")
+    # projected columns keep their source types
+    res = ctx.run(plan, pv.variant(exec="multi"))
+    cols = ctx.fetch(res)
+    ctx.free(res)
+    assert cols[0].dtype == np.int32 and cols[1].dtype == np.int64
 
 
 def test_project_golden_example(ctx):
