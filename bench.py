@@ -114,34 +114,43 @@ def ncu_traffic(workload: str):
 
 
 class ClockSampler:
-    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+    """nvidia-smi sampling of SM clocks and throttle reasons.  Samples carry a
+    host timestamp; summary() keeps those inside the marked timed window (or,
+    when the window was shorter than the sampling period, the samples of the
+    whole loaded phase since start_load())."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, period_ms: int = 20):
         self.index = index
+        self.period_ms = period_ms
         self.proc = None
         self.lines = []
+        self.t_load = self.t0 = self.t1 = None
 
-    def __enter__(self):
+    def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                                          "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True, bufsize=1)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t_end = time.time() + 10
+            while not self.lines and time.time() < t_end and self.proc.poll() is None:
+                time.sleep(0.01)
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
 
-    def __exit__(self, *a):
+    def stop(self):
         if self.proc:
+            time.sleep(2 * self.period_ms / 1000)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -149,23 +158,85 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
-            f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                mx = float(f[2])
-            except ValueError:
-                continue
-            for n, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
+
+        def parse(lo, hi):
+            sm, mx, reasons = [], None, set()
+            for ts, line in self.lines:
+                if lo is not None and not (lo <= ts <= hi):
+                    continue
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx = float(f[2])
+                except ValueError:
+                    continue
+                for n, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+            return sm, mx, reasons
+
+        window = "timed"
+        sm, mx, reasons = parse(self.t0, self.t1)
+        if not sm and self.t_load is not None:
+            window = "warmup+timed"
+            sm, mx, reasons = parse(self.t_load, self.t1)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm), "window": window}
+
+
+class NvmlSampler:
+    """SM clock and clock-event reasons read through NVML (ctypes) every
+    ~1 ms on a host thread while the timed window is open.  Read-only."""
+
+    BITS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
+
+    def __init__(self, index: int):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(index, ctypes.byref(self.h)) != 0:
+            raise OSError("no NVML handle")
+        self.reason_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = ctypes.c_uint()
+        self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(mx))
+        self.max_mhz = float(mx.value)
+        self.samples = []
+        self.on = False
+
+    def _loop(self):
+        ct = self.ct
+        mhz, rs = ct.c_uint(), ct.c_ulonglong()
+        while self.on:
+            self.lib.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(mhz))
+            self.reason_fn(self.h, ct.byref(rs))
+            self.samples.append((float(mhz.value), int(rs.value)))
+            time.sleep(0.001)
+
+    def __enter__(self):
+        self.on = True
+        self.t = threading.Thread(target=self._loop, daemon=True)
+        self.t.start()
+        return self
+
+    def __exit__(self, *a):
+        self.on = False
+        self.t.join()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unsampled"], "samples": 0}
+        reasons = sorted({n for _, r in self.samples for b, n in self.BITS.items() if r & b})
+        return {"sm_mhz": statistics.median(m for m, _ in self.samples), "sm_max_mhz": self.max_mhz,
+                "reasons": reasons, "samples": len(self.samples), "window": "timed", "source": "nvml"}
 
 
 def dist_env():
@@ -272,7 +343,9 @@ def run_pv(args):
         assert int(first[nk + 7].sum()) == passing, "count invariant failed"
     stream = ctx.stream
     ctx.set_kernel_timing(True)
-    for _ in range(args.warmup):
+    clk = ClockSampler(local).start()
+    clk.t_load = time.time()
+    for _ in range(max(args.warmup, 1)):
         ctx.lib.pv_l2_flush(ctx.h)
         ctx.rerun(res)
     ctx.sync()
@@ -282,15 +355,25 @@ def run_pv(args):
     launches_per_step = 0
     barrier(dist)
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        for i in range(args.steps):
-            ctx.lib.pv_l2_flush(ctx.h)  # cold L2 before every step (outside the timed events)
-            starts[i].record(stream)
-            ctx.rerun(res)
-            ends[i].record(stream)
-            launches_per_step = ctx.last_launch_count()
-            kernel_ms.append(ctx.kernel_times())
-        torch.cuda.synchronize()
+    try:
+        nv = NvmlSampler(local)
+    except OSError:
+        nv = None
+    if nv:
+        nv.__enter__()
+    clk.t0 = time.time()
+    for i in range(args.steps):
+        ctx.lib.pv_l2_flush(ctx.h)  # cold L2 before every step (outside the timed events)
+        starts[i].record(stream)
+        ctx.rerun(res)
+        ends[i].record(stream)
+        launches_per_step = ctx.last_launch_count()
+        kernel_ms.append(ctx.kernel_times())
+    torch.cuda.synchronize()
+    clk.t1 = time.time()
+    if nv:
+        nv.__exit__()
+    clk.stop()
     barrier(dist)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_s = max_over_ranks(dist, sum(step_ms) / 1000.0)
@@ -336,7 +419,7 @@ def run_pv(args):
         "e2e": {"value": rows * world * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": (launches_per_step + 1) * args.steps,
-        "clocks": clk.summary(),
+        "clocks": nv.summary() if nv and nv.samples else clk.summary(),
     }
     if rank == 0 and not args.no_cpu_baseline:
         rate, cores, n = cpu_oracle_rate(plan, tables, args.cpu_budget, rows)
@@ -353,7 +436,7 @@ def run_pv(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="pv", choices=["pv", "reference"])
     ap.add_argument("--workload", default="lowcard", choices=sorted(WORKLOADS))
