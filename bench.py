@@ -53,12 +53,12 @@ WORKLOADS = {
 
 # Variant per workload (measured best so far; the autotuner refreshes these).
 TUNED = {
-    "lowcard": dict(agg="local", ht="perfect", threads_per_table=1, pred="branch", access="grid",
-                    items_per_thread=2, block=256),
-    "filter_agg": dict(pred="branch", access="grid", items_per_thread=2, block=256),
-    "filter_project": dict(exec="multi", pred="branch", access="grid", items_per_thread=4, block=256),
-    "keyval": dict(agg="global", ht="perfect", pred="branch", access="grid", items_per_thread=2, block=256),
-    "star": dict(agg="local", ht="perfect", pred="branch", access="grid", items_per_thread=2, block=256),
+    "lowcard": dict(agg="local", ht="perfect", threads_per_table=1, pred="predicated", access="grid",
+                    items_per_thread=1, block=256, prefetch=1),
+    "filter_agg": dict(pred="branch", access="grid", items_per_thread=4, block=512, grid_mult=2),
+    "filter_project": dict(exec="single", pred="branch", access="grid", items_per_thread=4, block=128),
+    "keyval": dict(agg="local", ht="perfect", pred="branch", access="grid", items_per_thread=1, block=512),
+    "star": dict(agg="global", ht="perfect", pred="branch", access="grid", items_per_thread=1, block=512),
 }
 
 

@@ -153,7 +153,8 @@ typedef struct {
   int32_t items_per_thread;  /* unroll: 4-row items per thread per trip, 1, 2 or 4 (0 = 2) */
   int32_t threads_per_table; /* PV_AGG_LOCAL: 1 = thread-private tables, 0 = one per CTA */
   int32_t cuckoo_k;          /* aggregation cuckoo hash functions (0 = 3) */
-  int32_t reserved;
+  int32_t prefetch;          /* grid-stride predicated pipelines: bulk-prefetch each warp's column
+                                chunks this many loop trips ahead into L2 (0 = off) */
   uint64_t seed;             /* aggregation hash seeds */
 } pv_variant;
 

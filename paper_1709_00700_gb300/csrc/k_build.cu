@@ -78,7 +78,7 @@ __device__ __forceinline__ void cuckoo_put(const DevHT& h, uint64_t val, int max
   set_error(err, PV_ERR_CUCKOO_CYCLE);
 }
 
-__global__ void k_build(const BuildParams bp) {
+__global__ void k_build(const __grid_constant__ BuildParams bp) {
   const BuildInput& in = bp.in;
   const DevHT& h = bp.ht;
   unsigned long long* slots = reinterpret_cast<unsigned long long*>(h.slots);
@@ -125,7 +125,7 @@ __global__ void k_build(const BuildParams bp) {
 
 // Duplicate check of a cuckoo table: every key stays within its k candidate
 // slots, so a key found in two of them was inserted twice.
-__global__ void k_cuckoo_dupcheck(const DevHT h, int32_t* err) {
+__global__ void k_cuckoo_dupcheck(const __grid_constant__ DevHT h, int32_t* err) {
   const unsigned long long* slots = reinterpret_cast<const unsigned long long*>(h.slots);
   for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < h.cap;
        p += static_cast<int64_t>(gridDim.x) * blockDim.x) {

@@ -104,19 +104,45 @@ __device__ __forceinline__ void global_cuckoo_insert(const GroupOut& g, uint64_t
   set_error(err, PV_ERR_CUCKOO_CYCLE);
 }
 
-// Adds one row's aggregate codes (count last) into a slot with atomics.
-template <int NA>
-__device__ __forceinline__ void slot_atomic_add(unsigned long long* v, const uint64_t (&c)[NA + 1],
-                                                const int32_t (&func)[PV_MAX_AGGS]) {
-#pragma unroll
-  for (int a = 0; a < NA; ++a) {
-    if (func[a] == PV_SUM || func[a] == PV_COUNT) {
-      if (c[a]) atomicAdd(v + a, static_cast<unsigned long long>(c[a]));
-    } else if (c[a]) {
-      atomicMax(v + a, static_cast<unsigned long long>(c[a]));
-    }
+// Index of the first COUNT aggregate of a shape, -1 if it has none.
+template <class A>
+constexpr int count_index() {
+  for (int i = 0; i < A::N; ++i)
+    if (A::func_of[i] == PV_COUNT) return i;
+  return -1;
+}
+
+// 64-bit add into shared memory with 32-bit atomics: fetch-add the low word,
+// add the high word (plus the carry out of the low word) only when it is not
+// zero.  Exact modulo 2^64, also under concurrency (each adder's carry comes
+// from its own fetch-add).
+__device__ __forceinline__ void shared_add64(unsigned long long* p, uint64_t x) {
+  unsigned int* w = reinterpret_cast<unsigned int*>(p);
+  const unsigned int lo = static_cast<unsigned int>(x);
+  unsigned int hi = static_cast<unsigned int>(x >> 32);
+  if (lo) {
+    const unsigned int old = atomicAdd(w, lo);
+    hi += (old + lo < old) ? 1u : 0u;
   }
-  if (c[NA]) atomicAdd(v + NA, static_cast<unsigned long long>(c[NA]));
+  if (hi) atomicAdd(w + 1, hi);
+}
+
+// Adds one row's aggregate codes into a slot with atomics; zero codes (dead
+// rows, empty MIN/MAX) cost no atomic.  The hidden row count (last word) is
+// kept only when the shape has no COUNT aggregate.  SHARED: the slot is in
+// shared memory (32-bit atomics for the sums).
+template <class SH, bool SHARED = false>
+__device__ __forceinline__ void slot_atomic_add(unsigned long long* v, const uint64_t (&c)[SH::Aggs::N + 1]) {
+  using A = typename SH::Aggs;
+  static_for<A::N + 1>([&](auto a) {
+    constexpr int I = decltype(a)::value;
+    constexpr int F = I < A::N ? A::func_of[I < A::N ? I : 0] : PV_COUNT;
+    if constexpr (I == A::N && count_index<A>() >= 0) return;
+    if (c[I]) {
+      if constexpr (SHARED && (F == PV_SUM || F == PV_COUNT)) shared_add64(v + I, c[I]);
+      else acc_atomic<F>(v + I, c[I]);
+    }
+  });
 }
 
 // Aggregate codes of row r: SUM/COUNT values, MIN/MAX order codes, row count;
@@ -158,18 +184,36 @@ struct SinkGlobalHash {
     if (s > static_cast<uint64_t>(g.cap)) return;
     uint64_t c[NA + 1];
     row_codes<SH>(it, kp, r, live ? ~0ull : 0ull, c);
-    slot_atomic_add<NA>(g.vals + s * g.stride, c, gd.func);
+    slot_atomic_add<SH>(g.vals + s * g.stride, c);
   }
   __device__ void finish() {}
 };
 
+// Perfect-array slot of row r: parts minus their minima, row-major over the
+// part spans.  Keys made of 32-bit sources use 32-bit arithmetic (the domain
+// is at most 2^28 slots); unsigned differences wrap below the minimum.
 template <class SH>
 __device__ __forceinline__ uint64_t row_perfect_index(const GroupDesc& gd, Item<SH>& it, const KParams& kp, int r,
                                                       bool& ok) {
-  const int64_t p0 = key_part<SH, 0>(it, kp, r);
-  int64_t p1 = 0;
-  if constexpr (SH::Key::N == 2) p1 = key_part<SH, 1>(it, kp, r);
-  return perfect_index(gd, p0, p1, ok);
+  using K = typename SH::Key;
+  constexpr bool narrow = KeyPart32<SH, typename At<0, typename K::L>::type>::value &&
+                          (K::N == 1 || KeyPart32<SH, typename At<K::N - 1, typename K::L>::type>::value);
+  if constexpr (narrow) {
+    const uint32_t a = static_cast<uint32_t>(key_part<SH, 0>(it, kp, r)) - static_cast<uint32_t>(gd.key_min[0]);
+    ok = a < static_cast<uint32_t>(gd.key_span[0]);
+    if constexpr (K::N == 1) {
+      return a;
+    } else {
+      const uint32_t b = static_cast<uint32_t>(key_part<SH, 1>(it, kp, r)) - static_cast<uint32_t>(gd.key_min[1]);
+      ok = ok && b < static_cast<uint32_t>(gd.key_span[1]);
+      return a * static_cast<uint32_t>(gd.key_span[1]) + b;
+    }
+  } else {
+    const int64_t p0 = key_part<SH, 0>(it, kp, r);
+    int64_t p1 = 0;
+    if constexpr (K::N == 2) p1 = key_part<SH, 1>(it, kp, r);
+    return perfect_index(gd, p0, p1, ok);
+  }
 }
 
 template <class SH>
@@ -187,7 +231,7 @@ struct SinkGlobalPerfect {
     }
     uint64_t c[NA + 1];
     row_codes<SH>(it, kp, r, live ? ~0ull : 0ull, c);
-    slot_atomic_add<NA>(g.vals + s * g.stride, c, gd.func);
+    slot_atomic_add<SH>(g.vals + s * g.stride, c);
   }
   __device__ void finish() {}
 };
@@ -214,7 +258,7 @@ struct SinkLocalPerfect {
     }
     uint64_t c[NA + 1];
     row_codes<SH>(it, kp, r, live ? ~0ull : 0ull, c);
-    slot_atomic_add<NA>(sm + s * g.stride, c, gd.func);
+    slot_atomic_add<SH, true>(sm + s * g.stride, c);
   }
   __device__ void finish() {
     __syncthreads();
@@ -229,51 +273,80 @@ struct SinkLocalPerfect {
   }
 };
 
-// Thread-private perfect arrays (M = 1): thread t owns the words
-// sm[w * blockDim + t]; no atomics until the CTA epilogue.
+// Thread-private perfect arrays (M = 1): no atomics until the CTA epilogue.
+// A slot holds SW words (the aggregates, the row count unless a COUNT
+// aggregate already counts rows, padded to an even count) stored as SW / 2
+// 16-byte pairs, interleaved by thread: pair j of slot s of thread t is at
+// 16-byte unit (s * SW / 2 + j) * blockDim + t, so the 8 lanes of a memory
+// phase always touch 8 distinct bank groups, whatever slot each lane updates.
+// Slot cap is a scratch slot: a dead row (software predication) updates it
+// instead of masking every value.
 template <class SH>
 struct SinkThreadPerfect {
-  static constexpr int NA = SH::Aggs::N;
-  const GroupDesc& gd; const GroupOut& g; int32_t* err; unsigned long long* sm;
+  using A = typename SH::Aggs;
+  static constexpr int NA = A::N;
+  static constexpr int CA = count_index<A>();
+  static constexpr int SW = ((CA >= 0 ? NA : NA + 1) + 1) & ~1;
+  static constexpr int SP = SW / 2;
+  static __host__ __device__ int64_t units_per_thread(int64_t cap) { return (cap + 1) * SP; }
+  template <int W>
+  static __device__ __forceinline__ constexpr int word_func() {
+    if constexpr (W < NA) return A::func_of[W];
+    else return PV_SUM;
+  }
+  const GroupDesc& gd; const GroupOut& g; int32_t* err; ulonglong2* sm;
   __device__ SinkThreadPerfect(const GroupDesc& d, const GroupOut& o, int32_t* e, unsigned long long* s)
-      : gd(d), g(o), err(e), sm(s) {}
+      : gd(d), g(o), err(e), sm(reinterpret_cast<ulonglong2*>(s)) {}
   __device__ void init() {
-    const int64_t words = g.cap * g.stride;
-    for (int64_t w = 0; w < words; ++w) sm[w * blockDim.x + threadIdx.x] = 0;
+    const int64_t n = units_per_thread(g.cap);
+    for (int64_t u = 0; u < n; ++u) sm[u * blockDim.x + threadIdx.x] = make_ulonglong2(0, 0);
   }
   __device__ __forceinline__ void add(Item<SH>& it, const KParams& kp, int r, bool live) {
     bool ok;
     uint64_t s = row_perfect_index<SH>(gd, it, kp, r, ok);
-    if (!ok) {
-      if (live) { set_error(err, PV_ERR_KEY_OUT_OF_RANGE); return; }
-      s = 0;
-    }
-    uint64_t c[NA + 1];
-    row_codes<SH>(it, kp, r, live ? ~0ull : 0ull, c);
-    unsigned long long* p = sm + s * g.stride * blockDim.x + threadIdx.x;
-#pragma unroll
-    for (int a = 0; a <= NA; ++a) {
-      const bool add = a == NA || gd.func[a] == PV_SUM || gd.func[a] == PV_COUNT;
-      const uint64_t cur = p[a * blockDim.x];
-      p[a * blockDim.x] = add ? cur + c[a] : (c[a] > cur ? c[a] : cur);
-    }
+    if (!ok && live) set_error(err, PV_ERR_KEY_OUT_OF_RANGE);
+    s = (ok && live) ? s : static_cast<uint64_t>(g.cap);
+    uint64_t v[SW];
+    static_for<SW>([&](auto w) {
+      constexpr int I = decltype(w)::value;
+      if constexpr (I < NA) {
+        using AG = typename At<(I < NA ? I : 0), typename A::L>::type;
+        v[I] = acc_code<AG::func>(agg_value<AG>(it, kp, r));
+      } else {
+        v[I] = (CA < 0 && I == NA) ? 1ull : 0ull;
+      }
+    });
+    ulonglong2* p = sm + static_cast<uint32_t>(s) * SP * blockDim.x + threadIdx.x;
+    static_for<SP>([&](auto j) {
+      constexpr int J = decltype(j)::value;
+      ulonglong2 c = p[J * blockDim.x];
+      c.x = acc_combine<word_func<2 * J>()>(c.x, v[2 * J]);
+      c.y = acc_combine<word_func<2 * J + 1>()>(c.y, v[2 * J + 1]);
+      p[J * blockDim.x] = c;
+    });
   }
   __device__ void finish() {
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int64_t words = g.cap * g.stride;
-    for (int64_t w = warp; w < words; w += nwarps) {
-      const int a = static_cast<int>(w % g.stride);
-      const bool add = a == NA || gd.func[a] == PV_SUM || gd.func[a] == PV_COUNT;
+    const unsigned long long* w64 = reinterpret_cast<const unsigned long long*>(sm);
+    constexpr int used = CA >= 0 ? NA : NA + 1;
+    for (int64_t w = warp; w < g.cap * SW; w += nwarps) {
+      const int64_t slot = w / SW;
+      const int a = static_cast<int>(w % SW);
+      if (a >= used) continue;
+      const bool add = a >= NA || gd.func[a] == PV_SUM || gd.func[a] == PV_COUNT;
+      const int64_t unit = slot * SP + a / 2;
       uint64_t v = 0;
       for (int t = lane; t < static_cast<int>(blockDim.x); t += 32) {
-        const uint64_t x = sm[w * blockDim.x + t];
+        const uint64_t x = w64[2 * (unit * blockDim.x + t) + (a & 1)];
         v = add ? v + x : (x > v ? x : v);
       }
       v = add ? warp_reduce<PV_SUM>(v) : warp_reduce<PV_MAX>(v);
       if (lane == 0 && v) {
-        if (add) atomicAdd(g.vals + w, static_cast<unsigned long long>(v));
-        else atomicMax(g.vals + w, static_cast<unsigned long long>(v));
+        unsigned long long* dst = g.vals + slot * g.stride;
+        if (a == NA) atomicAdd(dst + NA, static_cast<unsigned long long>(v));  // row count word
+        else if (add) atomicAdd(dst + a, static_cast<unsigned long long>(v));
+        else atomicMax(dst + a, static_cast<unsigned long long>(v));
       }
     }
   }
@@ -303,14 +376,14 @@ struct SinkLocalHash {
         unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(lk + idx);
         if (cur == kEmpty64) cur = atomicCAS(lk + idx, kEmpty64, static_cast<unsigned long long>(key));
         if (cur == kEmpty64 || cur == key) {
-          slot_atomic_add<NA>(lv + static_cast<uint64_t>(idx) * g.stride, c, gd.func);
+          slot_atomic_add<SH, true>(lv + static_cast<uint64_t>(idx) * g.stride, c);
           return;
         }
         idx = (idx + 1) & mask;
       }
     }
     const uint64_t s = global_slot<GM>(g, key, err);
-    if (s <= static_cast<uint64_t>(g.cap)) slot_atomic_add<NA>(g.vals + s * g.stride, c, gd.func);
+    if (s <= static_cast<uint64_t>(g.cap)) slot_atomic_add<SH>(g.vals + s * g.stride, c);
   }
   __device__ void finish() {
     __syncthreads();
@@ -320,9 +393,9 @@ struct SinkLocalHash {
       uint64_t c[NA + 1];
 #pragma unroll
       for (int a = 0; a <= NA; ++a) c[a] = lv[static_cast<uint64_t>(i) * g.stride + a];
-      if (!c[NA]) continue;
+      if (!c[count_index<typename SH::Aggs>() >= 0 ? count_index<typename SH::Aggs>() : NA]) continue;
       const uint64_t s = global_slot<GM>(g, key, err);
-      if (s <= static_cast<uint64_t>(g.cap)) slot_atomic_add<NA>(g.vals + s * g.stride, c, gd.func);
+      if (s <= static_cast<uint64_t>(g.cap)) slot_atomic_add<SH>(g.vals + s * g.stride, c);
     }
   }
 };
@@ -331,14 +404,12 @@ struct SinkLocalHash {
 // Kernels
 // ---------------------------------------------------------------------------
 template <class SH, bool PRED, bool CHUNK, int U, class Sink>
-__global__ void __maxnreg__(128) k_group(const KParams kp, const GroupDesc gd, const GroupOut g) {
+__global__ void __maxnreg__(128) k_group(const __grid_constant__ KParams kp, const __grid_constant__ GroupDesc gd, const __grid_constant__ GroupOut g) {
   extern __shared__ unsigned long long smem[];
   if (blockIdx.x == 0 && threadIdx.x == 0) *g.out_count = 0;  // extraction runs after this kernel
   Sink sink(gd, g, kp.err, smem);
   sink.init();
-  for_items<CHUNK, U>(kp.n_items, [&](const int64_t (&idx)[U]) {
-    Item<SH> it[U];
-    eval_items<SH, PRED, U>(it, kp, idx);
+  auto consume = [&](Item<SH> (&it)[U]) {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (!PRED && !it[u].mask) continue;
@@ -348,14 +419,23 @@ __global__ void __maxnreg__(128) k_group(const KParams kp, const GroupDesc gd, c
         if (PRED ? r < it[u].nvalid : live) sink.add(it[u], kp, r, live);
       }
     }
-  });
+  };
+  if constexpr (PRED) {
+    for_items_pipelined<SH, CHUNK, U>(kp, consume);
+  } else {
+    for_items_pf<SH, CHUNK, U>(kp, [&](const int64_t (&idx)[U]) {
+      Item<SH> it[U];
+      eval_items<SH, PRED, U>(it, kp, idx);
+      consume(it);
+    });
+  }
   sink.finish();
 }
 
 // Key pass of the multi-pass strategy: insert the group key of every row
 // (every valid row when predicated) into the global linear or cuckoo table.
 template <class SH, bool PRED, bool CHUNK, int U, int HTK>
-__global__ void __maxnreg__(128) k_group_keys(const KParams kp, const GroupDesc gd, const GroupOut g) {
+__global__ void __maxnreg__(128) k_group_keys(const __grid_constant__ KParams kp, const __grid_constant__ GroupDesc gd, const __grid_constant__ GroupOut g) {
   for_items<CHUNK, U>(kp.n_items, [&](const int64_t (&idx)[U]) {
     Item<SH> it[U];
     eval_items<SH, PRED, U>(it, kp, idx);
@@ -376,9 +456,9 @@ __global__ void __maxnreg__(128) k_group_keys(const KParams kp, const GroupDesc 
 
 // Removes cuckoo duplicates: a key is kept only at the first of its k
 // candidate slots that holds it.
-__global__ void k_cuckoo_dedupe(const GroupOut g);
+__global__ void k_cuckoo_dedupe(const __grid_constant__ GroupOut g);
 // Compacts non-empty slots into the dense result columns and empties them.
-__global__ void k_extract(const GroupDesc gd, const GroupOut g);
+__global__ void k_extract(const __grid_constant__ GroupDesc gd, const __grid_constant__ GroupOut g);
 pv_status launch_dedupe_extract(const LaunchCfg& c, const GroupDesc& gd, const GroupOut& g, bool dedupe);
 
 template <class SH> using SinkGInsert = SinkGlobalHash<SH, G_INSERT>;
@@ -457,7 +537,7 @@ static pv_status launch_group(const LaunchCfg& c, const KParams& kp, const Group
     if (!local) {
       s = run_group<SH, UMASK, SinkGlobalPerfect>(c, kp, gd, g, 0);
     } else if (v.threads_per_table == 1) {
-      const size_t smem = static_cast<size_t>(g.cap) * slot_bytes * c.block;
+      const size_t smem = static_cast<size_t>(SinkThreadPerfect<SH>::units_per_thread(g.cap)) * 16 * c.block;
       if (smem > 200 * 1024) return PV_ERR_UNSUPPORTED;
       s = run_group<SH, UMASK, SinkThreadPerfect>(c, kp, gd, g, smem);
     } else {

@@ -5,7 +5,7 @@
 
 namespace pv {
 
-__global__ void k_cuckoo_dedupe(const GroupOut g) {
+__global__ void k_cuckoo_dedupe(const __grid_constant__ GroupOut g) {
   for (int64_t s = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; s < g.cap;
        s += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const unsigned long long key = __ldcg(g.keys + s);
@@ -28,7 +28,7 @@ __device__ __forceinline__ int64_t decode_agg(int func, uint64_t c) {
 
 // Warp-uniform sweep over the cap + 1 slots; non-empty slots are appended to
 // the result columns with one atomicAdd per warp, then cleared.
-__global__ void k_extract(const GroupDesc gd, const GroupOut g) {
+__global__ void k_extract(const __grid_constant__ GroupDesc gd, const __grid_constant__ GroupOut g) {
   const int64_t total = g.cap + 1;
   const int lane = threadIdx.x & 31;
   const int64_t T = static_cast<int64_t>(gridDim.x) * blockDim.x;
@@ -42,14 +42,14 @@ __global__ void k_extract(const GroupDesc gd, const GroupOut g) {
     unsigned long long* v = g.vals + s * g.stride;
     if (s < total) {
       if (perfect) {
-        occ = s < g.cap && v[na] != 0;
+        occ = s < g.cap && v[gd.count_word] != 0;
         dirty = occ;
       } else if (s < g.cap) {
         key = g.keys[s];
         dirty = key != kEmpty64;
-        occ = dirty && v[na] != 0;
+        occ = dirty && v[gd.count_word] != 0;
       } else {
-        occ = dirty = v[na] != 0;
+        occ = dirty = v[gd.count_word] != 0;
       }
     }
     const unsigned ball = __ballot_sync(0xffffffffu, occ);
@@ -98,12 +98,14 @@ pv_status launch_dedupe_extract(const LaunchCfg& c, const GroupDesc& gd, const G
 
 void register_group_lowcard();
 void register_group_keyval();
+void register_group_keyval_f();
 void register_group_star();
 void register_group_join2();
 
 void register_group_shapes() {
   register_group_lowcard();
   register_group_keyval();
+  register_group_keyval_f();
   register_group_star();
   register_group_join2();
 }

@@ -11,6 +11,6 @@ using ShLowcard =
                Sum<Mul<X<4>, CMX<5, 1>, XPC<6, 2>>>, Sum<Mul<X<3>, X<4>>>, Count>,
           Proj<>>;
 
-void register_group_lowcard() { reg_grouped<ShLowcard>(); }
+void register_group_lowcard() { reg_grouped<ShLowcard, 1>(); }
 
 }  // namespace pv

@@ -7,6 +7,6 @@ namespace pv {
 using ShStar4 = Shape<Cols<TI32, TI32, TI32, TI32, TI64>, Where<>, Probes<0, 1, 2, 3>, Key<PL<2, 0>, PL<3, 0>>,
                       Aggs<Sum<Mul<X<4>>>, Count>, Proj<>>;
 
-void register_group_star() { reg_grouped<ShStar4, 3>(); }
+void register_group_star() { reg_grouped<ShStar4, 1>(); }
 
 }  // namespace pv

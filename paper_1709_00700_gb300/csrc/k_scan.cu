@@ -16,16 +16,14 @@ namespace pv {
 // aggregate; the last CTA decodes the result and re-zeroes the accumulators.
 // ---------------------------------------------------------------------------
 template <class SH, bool PRED, bool CHUNK, int U>
-__global__ void __maxnreg__(128) k_aggregate(const KParams kp, const AggOut out) {
+__global__ void __maxnreg__(128) k_aggregate(const __grid_constant__ KParams kp, const __grid_constant__ AggOut out) {
   using A = typename SH::Aggs;
   constexpr int NA = A::N;
   uint64_t acc[NA + 1];
 #pragma unroll
   for (int a = 0; a <= NA; ++a) acc[a] = 0;
 
-  for_items<CHUNK, U>(kp.n_items, [&](const int64_t (&idx)[U]) {
-    Item<SH> it[U];
-    eval_items<SH, PRED, U>(it, kp, idx);
+  auto consume = [&](Item<SH> (&it)[U]) {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
 #pragma unroll
@@ -49,7 +47,16 @@ __global__ void __maxnreg__(128) k_aggregate(const KParams kp, const AggOut out)
         }
       }
     }
-  });
+  };
+  if constexpr (PRED) {
+    for_items_pipelined<SH, CHUNK, U>(kp, consume);
+  } else {
+    for_items_pf<SH, CHUNK, U>(kp, [&](const int64_t (&idx)[U]) {
+      Item<SH> it[U];
+      eval_items<SH, PRED, U>(it, kp, idx);
+      consume(it);
+    });
+  }
 
   __shared__ unsigned long long red[32][NA + 1];
   __shared__ bool last;
@@ -153,7 +160,7 @@ __device__ __forceinline__ uint64_t block_excl_scan(uint64_t v, uint64_t* total)
 // output cursor (ballot-free: counts are scanned with shuffles), then each
 // lane writes its rows.  Output order is arbitrary across warps.
 template <class SH, bool PRED, bool CHUNK, int U>
-__global__ void __maxnreg__(128) k_project_sp(const KParams kp, const ProjOut out) {
+__global__ void __maxnreg__(128) k_project_sp(const __grid_constant__ KParams kp, const __grid_constant__ ProjOut out) {
   bool overflow = false;
   for_items_uniform<CHUNK, U>(kp.n_items, [&](const int64_t (&idx)[U]) {
     Item<SH> it[U];
@@ -222,7 +229,7 @@ __device__ __forceinline__ void for_tiles(int64_t n_tiles, F&& f) {
 }
 
 template <class SH, bool PRED, bool CHUNK, int U>
-__global__ void __maxnreg__(128) k_project_count(const KParams kp, const ProjOut out) {
+__global__ void __maxnreg__(128) k_project_count(const __grid_constant__ KParams kp, const __grid_constant__ ProjOut out) {
   for_tiles<CHUNK>(out.n_tiles, [&](int64_t tile) {
     int64_t idx[U];
     tile_items<CHUNK, U>(tile, idx);
@@ -238,7 +245,7 @@ __global__ void __maxnreg__(128) k_project_count(const KParams kp, const ProjOut
 }
 
 // Exclusive prefix sum over the tile counts (one CTA of 1024 threads).
-__global__ void __launch_bounds__(1024) k_tile_scan(const ProjOut out, int32_t* err) {
+__global__ void __launch_bounds__(1024) k_tile_scan(const __grid_constant__ ProjOut out, int32_t* err) {
   const int64_t n = out.n_tiles;
   const int64_t per = (n + blockDim.x - 1) / blockDim.x;
   const int64_t b = threadIdx.x * per;
@@ -259,7 +266,7 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const ProjOut out, int32_t* 
 }
 
 template <class SH, bool PRED, bool CHUNK, int U>
-__global__ void __maxnreg__(128) k_project_scatter(const KParams kp, const ProjOut out) {
+__global__ void __maxnreg__(128) k_project_scatter(const __grid_constant__ KParams kp, const __grid_constant__ ProjOut out) {
   static_assert(U <= 4, "16-bit scan fields hold at most 4 unroll slots");
   for_tiles<CHUNK>(out.n_tiles, [&](int64_t tile) {
     int64_t idx[U];

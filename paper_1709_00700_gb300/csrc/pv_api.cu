@@ -389,6 +389,7 @@ static pv_status resolve_launch(pv_ctx* c, const pv_variant& v, LaunchCfg& L) {
   if (v.pred != PV_BRANCH && v.pred != PV_PREDICATED) return fail(c, PV_ERR_INVALID_ARG, "bad pred mode");
   if (v.access != PV_GRID_STRIDE && v.access != PV_CHUNKED) return fail(c, PV_ERR_INVALID_ARG, "bad access");
   if (v.exec != PV_EXEC_SINGLE_PASS && v.exec != PV_EXEC_MULTI_PASS) return fail(c, PV_ERR_INVALID_ARG, "bad exec");
+  if (v.prefetch < 0 || v.prefetch > 16) return fail(c, PV_ERR_INVALID_ARG, "prefetch must be 0..16 trips");
   L.pred = v.pred == PV_PREDICATED;
   L.chunk = v.access == PV_CHUNKED;
   L.launches = &c->launches;
@@ -559,6 +560,9 @@ static pv_status alloc_result(pv_ctx* c, Result& r) {
   GroupDesc& gd = r.gd;
   gd.n_keys = k.n_keys;
   gd.n_aggs = k.n_aggs;
+  gd.count_word = k.n_aggs;
+  for (int i = k.n_aggs - 1; i >= 0; --i)
+    if (k.agg_func[i] == PV_COUNT) gd.count_word = i;
   for (int i = 0; i < k.n_aggs; ++i) gd.func[i] = k.agg_func[i];
   for (int i = 0; i < k.n_keys; ++i) gd.key64[i] = k.key_type[i] == PV_I64;
   // Key domains from column statistics / build payload statistics.
@@ -630,7 +634,8 @@ static pv_status launch_result(pv_ctx* c, Result& r) {
   c->launches = 0;
   c->kev_used = 0;
   r.rows_cached = -1;
-  const Canon& k = r.canon;
+  Canon& k = r.canon;
+  k.kp.prefetch = r.var.prefetch;
   if (k.mode == MODE_AGGREGATE) s = r.entry->aggregate(L, k.kp, r.agg);
   else if (k.mode == MODE_PROJECT) s = r.entry->project(L, k.kp, r.proj, r.var.exec);
   else s = r.entry->grouped(L, k.kp, r.gd, r.grp, r.var);

@@ -50,6 +50,7 @@ struct KParams {
   int64_t c[kMaxConsts];         // arithmetic constants, in order of appearance
   DevHT probe[PV_MAX_PROBES];
   int32_t* err;                  // device error word (first error wins)
+  int32_t prefetch;              // L2 bulk-prefetch distance in loop trips (0 = off)
 };
 
 __device__ __forceinline__ void set_error(int32_t* err, int32_t code) {

@@ -96,4 +96,156 @@ __device__ __forceinline__ void for_items_uniform(int64_t n_items, F&& f) {
   }
 }
 
+// Predicated pipelines split into a load phase (every column of every row
+// of the item) and a compute phase (filter bits, probes); with no branch
+// between them, the next items' loads can be issued before the current items
+// are consumed.
+template <class SH, int U>
+__device__ __forceinline__ void load_items_all(Item<SH> (&it)[U], const KParams& kp, const int64_t (&idx)[U]) {
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t left = kp.n_rows - idx[u] * 4;
+    it[u].nvalid = left >= 4 ? 4 : (left > 0 ? static_cast<int>(left) : 0);
+    it[u].mask = (1u << it[u].nvalid) - 1u;
+    load_slots<SH, SH::Where::slots | SH::Probes::slots | SH::rest_slots>(it[u], kp, idx[u]);
+  }
+}
+
+template <class SH, int U>
+__device__ __forceinline__ void filter_probe_items(Item<SH> (&it)[U], const KParams& kp) {
+  using W = typename SH::Where;
+  using JP = typename SH::Probes;
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+    static_for<W::N>([&](auto j) { it[u].mask &= pred_bits<SH, decltype(j)::value>(it[u], kp); });
+  static_for<JP::N>([&](auto j) {
+    constexpr int J = decltype(j)::value;
+    constexpr int S = JP::slot_of[J];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      auto& fk = VGet<S>::get(it[u].v);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        int32_t p = 0;
+        const bool hit = probe_key(kp.probe[J], static_cast<int64_t>(fk[r]), p);
+        it[u].pay[J][r] = p;
+        if (!hit) it[u].mask &= ~(1u << r);
+      }
+    }
+  });
+}
+
+// Bulk prefetch into L2 (TMA engine, no registers or shared memory used) of
+// the 128 rows a warp consumes at one trip, for every column the pipeline
+// loads.  Called by one lane; only whole in-bounds chunks are prefetched
+// (16-byte aligned: column bases are 16-byte aligned and 128 rows of any
+// column type are a multiple of 16 bytes).
+template <class SH>
+__device__ __forceinline__ void prefetch_warp_chunk(const KParams& kp, int64_t first_item) {
+  if (first_item < 0 || (first_item + 32) * 4 > kp.n_rows) return;
+  static_for<SH::Cols::N>([&](auto s) {
+    constexpr int S = decltype(s)::value;
+    using T = typename At<S, typename SH::Cols::L>::type::T;
+    const char* p = static_cast<const char*>(kp.col[S]) + first_item * 4 * static_cast<int64_t>(sizeof(T));
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(static_cast<uint32_t>(128 * sizeof(T)))
+                 : "memory");
+  });
+}
+
+// Grid-stride item loop (as for_items) that also bulk-prefetches into L2
+// the chunk its warp will read kp.prefetch trips later (lane 0 of a warp runs
+// every trip any lane of the warp runs).  Chunked access: no prefetch.
+template <class SH, bool CHUNK, int U, class F>
+__device__ __forceinline__ void for_items_pf(const KParams& kp, F&& f) {
+  const int pf = CHUNK ? 0 : kp.prefetch;
+  if (pf == 0) {
+    for_items<CHUNK, U>(kp.n_items, f);
+    return;
+  }
+  const int64_t T = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  auto prefetch = [&](int64_t k) {
+    if (lane == 0) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) prefetch_warp_chunk<SH>(kp, (t - lane) + (k * U + u) * T);
+    }
+  };
+  for (int d = 1; d <= pf; ++d) prefetch(d);
+  int64_t k = 0;
+  for (int64_t base = t; base < kp.n_items; base += U * T, ++k) {
+    prefetch(k + pf);
+    int64_t idx[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) idx[u] = base + u * T;
+    f(idx);
+  }
+}
+
+// Software-pipelined item loop of predicated pipelines: the loads of trip
+// k + 1 are in flight while trip k is filtered, probed and consumed (two
+// register buffers used in turn).  Trips and item indices are those of
+// for_items.
+template <class SH, bool CHUNK, int U, class F>
+__device__ __forceinline__ void for_items_pipelined(const KParams& kp, F&& consume) {
+  const int64_t n = kp.n_items;
+  const int64_t T = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  int64_t cbeg = 0, cend = 0;
+  if constexpr (CHUNK) {
+    const int64_t chunk = (n + T - 1) / T;
+    cbeg = t * chunk;
+    cend = cbeg + chunk < n ? cbeg + chunk : n;
+  }
+  auto valid = [&](int64_t k) { return CHUNK ? k * U < cend - cbeg : t + k * U * T < n; };
+  auto idx_of = [&](int64_t k, int64_t (&idx)[U]) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if constexpr (CHUNK) {
+        const int64_t i = cbeg + k * U + u;
+        idx[u] = i < cend ? i : n;
+      } else {
+        idx[u] = t + (k * U + u) * T;
+      }
+    }
+  };
+  if (!valid(0)) return;
+  const int lane = threadIdx.x & 31;
+  const int pf = CHUNK ? 0 : kp.prefetch;
+  // trip k of this warp covers items (t - lane) + (k * U + u) * T, 32 per u
+  auto prefetch = [&](int64_t k) {
+    if (lane == 0) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) prefetch_warp_chunk<SH>(kp, (t - lane) + (k * U + u) * T);
+    }
+  };
+  if (pf > 0) {
+    for (int d = 1; d <= pf; ++d) prefetch(d);
+  }
+  Item<SH> a[U], b[U];
+  int64_t ia[U], ib[U];
+  idx_of(0, ia);
+  load_items_all<SH, U>(a, kp, ia);
+  for (int64_t k = 0;; k += 2) {
+    if (pf > 0) prefetch(k + 1 + pf);
+    const bool more = valid(k + 1);
+    if (more) {
+      idx_of(k + 1, ib);
+      load_items_all<SH, U>(b, kp, ib);
+    }
+    filter_probe_items<SH, U>(a, kp);
+    consume(a);
+    if (!more) break;
+    if (pf > 0) prefetch(k + 2 + pf);
+    const bool more2 = valid(k + 2);
+    if (more2) {
+      idx_of(k + 2, ia);
+      load_items_all<SH, U>(a, kp, ia);
+    }
+    filter_probe_items<SH, U>(b, kp);
+    consume(b);
+    if (!more2) break;
+  }
+}
+
 }  // namespace pv

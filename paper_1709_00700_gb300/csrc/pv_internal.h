@@ -58,6 +58,8 @@ struct ProjOut {
 struct GroupDesc {
   int n_keys;
   int n_aggs;
+  int count_word;                // slot word holding the group's row count: the first
+                                 // COUNT aggregate, else word n_aggs (hidden count)
   int32_t func[PV_MAX_AGGS];
   int key64[PV_MAX_KEYS];        // key part is a 64-bit source (1 part only)
   int64_t key_min[PV_MAX_KEYS];  // perfect array: domain of each part
