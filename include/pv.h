@@ -251,6 +251,44 @@ pv_status pv_kernel_times(pv_ctx* ctx, float* ms, int32_t max, int32_t* n);
  * (bounded; for exercising the pv_sync watchdog). */
 pv_status pv_debug_spin(pv_ctx* ctx, int64_t ns);
 
+/* ---- allocation-free entry point ----------------------------------------- */
+
+/* Largest row count pv_filter_project_noalloc accepts. */
+#define PV_NOALLOC_MAX_ROWS (1LL << 28)
+
+/* The paper has no counterpart to this call; it exists for callers that cannot
+ * allocate device memory: code whose device memory is owned by another
+ * allocator (a database buffer pool or a framework's caching allocator that
+ * has reserved the device), and latency-critical code that cannot pay for
+ * cudaMalloc's device-wide synchronisation.  It needs no pv_ctx.
+ *
+ * Computes the multi-pass projection (count -> prefix sum -> scatter, as
+ * pv_run_pipeline with PV_EXEC_MULTI_PASS) of
+ *     SELECT a, price FROM t WHERE a_lo <= a <= a_hi AND b_lo <= b <= b_hi
+ * over n_rows rows of the int32 columns a, b and the int64 column price
+ * (device pointers, 16-byte aligned), writing the matching rows in input order
+ * to out_a / out_price (device, out_capacity rows each).  On the stream it
+ * writes *out_count (device int64) = rows written = min(matches,
+ * out_capacity) and *out_status (device int32) = PV_OK, or
+ * PV_ERR_OUTPUT_OVERFLOW when more rows matched than fit.
+ *
+ * It allocates nothing: its scratch (an error word plus per-tile counts and
+ * offsets, about 1 MB) is one statically sized array in device memory that
+ * every GPU loading this library holds until the process exits.  The first
+ * call on a device, with that device current, looks up the array's device
+ * address (cudaGetSymbolAddress) and caches it; make that first call before
+ * any stream capture.  Every call shares the one array and each clears what
+ * must start at zero, so calls that overlap on the GPU (other streams, other
+ * host threads) race: order them on one stream.
+ *
+ * Returns PV_ERR_INVALID_ARG for n_rows outside [0, PV_NOALLOC_MAX_ROWS], a
+ * negative capacity, null or misaligned pointers; PV_ERR_CUDA if a CUDA call
+ * fails; otherwise PV_OK once the work is enqueued (asynchronous). */
+pv_status pv_filter_project_noalloc(const int32_t* a, const int32_t* b, const int64_t* price, int64_t n_rows,
+                                    int64_t a_lo, int64_t a_hi, int64_t b_lo, int64_t b_hi, int32_t* out_a,
+                                    int64_t* out_price, int64_t out_capacity, int64_t* out_count,
+                                    int32_t* out_status, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -5,6 +5,8 @@
 //   PROJECT multi pass (Section 4.1 fine-grained strategy: a filter kernel
 //     counts matches, a prefix sum yields unique write positions, a
 //     projection kernel repeats filter and probes and writes).
+#include <mutex>
+
 #include "pv_eval.cuh"
 
 namespace pv {
@@ -431,4 +433,111 @@ void register_scan_shapes() {
   reg_aggregate<ShKeyValTotals>();
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free multi-pass projection.  Same kernels as the multi-pass
+// PROJECT above (fixed launch shape: 256 threads, 4 items per thread,
+// branched, coalesced), but its scratch -- the error word and the per-tile
+// match counts and write offsets -- lives in one file-scope device array
+// instead of memory from an allocator.  Every GPU that loads this library
+// holds the array until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNoAllocBlock = 256;
+constexpr int kNoAllocU = 4;
+constexpr int64_t kNoAllocTileRows = 4LL * kNoAllocBlock * kNoAllocU;
+constexpr int64_t kNoAllocMaxTiles = (PV_NOALLOC_MAX_ROWS + kNoAllocTileRows - 1) / kNoAllocTileRows;
+constexpr int64_t kNoAllocHeader = 32;  // words: [0] error word (int32), rest unused padding
+
+// Scratch of every call: header, then tile counts, then tile offsets (int64).
+__device__ __align__(256) int64_t g_noalloc_scratch[kNoAllocHeader + 2 * kNoAllocMaxTiles];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+int64_t* g_noalloc_addr[kNoAllocMaxDevices];  // device address of the array, per device
+int g_noalloc_sms[kNoAllocMaxDevices];
+
+// Device address of the scratch array on the current device.  In host code
+// the array's name is only a host-side stand-in, so the address is looked up
+// once per device (with that device current) and cached.
+pv_status noalloc_scratch(int64_t** addr, int* sms) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return PV_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return PV_ERR_CUDA;
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PV_ERR_CUDA;
+    g_noalloc_addr[dev] = static_cast<int64_t*>(p);
+    g_noalloc_sms[dev] = n;
+  }
+  *addr = g_noalloc_addr[dev];
+  *sms = g_noalloc_sms[dev];
+  return PV_OK;
+}
+
+void clamp_i32_range(int64_t& lo, int64_t& hi) {
+  if (lo > hi) { lo = 1; hi = 0; return; }
+  lo = lo < INT32_MIN ? INT32_MIN : lo;
+  hi = hi > INT32_MAX ? INT32_MAX : hi;
+  if (lo > hi) { lo = 1; hi = 0; }
+}
+
+}  // namespace
 }  // namespace pv
+
+extern "C" pv_status pv_filter_project_noalloc(const int32_t* a, const int32_t* b, const int64_t* price,
+                                                int64_t n_rows, int64_t a_lo, int64_t a_hi, int64_t b_lo,
+                                                int64_t b_hi, int32_t* out_a, int64_t* out_price,
+                                                int64_t out_capacity, int64_t* out_count, int32_t* out_status,
+                                                void* stream) {
+  using namespace pv;
+  if (n_rows < 0 || n_rows > PV_NOALLOC_MAX_ROWS || out_capacity < 0) return PV_ERR_INVALID_ARG;
+  if (!out_count || !out_status) return PV_ERR_INVALID_ARG;
+  if (n_rows > 0 && (!a || !b || !price)) return PV_ERR_INVALID_ARG;
+  if (out_capacity > 0 && (!out_a || !out_price)) return PV_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(price)) % 16)
+    return PV_ERR_INVALID_ARG;
+  int64_t* scratch = nullptr;
+  int sms = 0;
+  pv_status st = noalloc_scratch(&scratch, &sms);
+  if (st != PV_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  KParams kp{};
+  kp.n_rows = n_rows;
+  kp.n_items = (n_rows + 3) / 4;
+  kp.col[0] = a;
+  kp.col[1] = b;
+  kp.col[2] = price;
+  clamp_i32_range(a_lo, a_hi);
+  clamp_i32_range(b_lo, b_hi);
+  kp.lo[0] = a_lo;
+  kp.hi[0] = a_hi;
+  kp.lo[1] = b_lo;
+  kp.hi[1] = b_hi;
+  kp.err = reinterpret_cast<int32_t*>(scratch);
+  ProjOut out{};
+  out.col[0] = out_a;
+  out.col[1] = out_price;
+  out.capacity = out_capacity;
+  out.count = out_count;
+  out.n_tiles = (kp.n_items + kNoAllocBlock * kNoAllocU - 1) / (kNoAllocBlock * kNoAllocU);
+  if (out.n_tiles < 1) out.n_tiles = 1;
+  out.tile_count = scratch + kNoAllocHeader;
+  out.tile_offset = scratch + kNoAllocHeader + kNoAllocMaxTiles;
+  // the array keeps the previous call's contents: clear the error word
+  if (cudaMemsetAsync(scratch, 0, sizeof(int32_t), s) != cudaSuccess) return PV_ERR_CUDA;
+  int launches = 0;
+  LaunchCfg c{};
+  c.stream = s;
+  c.sm_count = sms;
+  c.block = kNoAllocBlock;
+  c.U = kNoAllocU;
+  c.launches = &launches;
+  st = launch_proj_t<ShFilterProj, false, false, kNoAllocU>(c, kp, out, PV_EXEC_MULTI_PASS);
+  if (st != PV_OK) return st;
+  if (cudaMemcpyAsync(out_status, scratch, sizeof(int32_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return PV_ERR_CUDA;
+  return PV_OK;
+}
