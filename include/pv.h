@@ -251,6 +251,40 @@ pv_status pv_kernel_times(pv_ctx* ctx, float* ms, int32_t max, int32_t* n);
  * (bounded; for exercising the pv_sync watchdog). */
 pv_status pv_debug_spin(pv_ctx* ctx, int64_t ns);
 
+/* ---- cost model --------------------------------------------------------- */
+
+/* A small fp32 network that predicts a variant's log run time from plan
+ * features, column statistics and variant features, so that the variant of
+ * each query can be chosen per query (the run-time optimizer Section 9.4
+ * leaves to future work) instead of one heuristic per workload (Section
+ * 8.3).  With F features (1..PV_MLP_MAX_FEATURES) and H = PV_MLP_HIDDEN:
+ *     xh = (x - mu) / sigma;  z1 = xh W1 + b1;  h1 = relu(z1)
+ *     z2 = h1 W2 + b2;        h2 = relu(z2);    y = h2 w3 + b3
+ * params is one float vector of F*H + H + H*H + H + H + 1 values in the order
+ * W1 (F x H row-major), b1, W2 (H x H row-major), b2, w3, b3.  All pointers
+ * are device memory owned by the caller; every call enqueues on the ctx
+ * stream and allocates nothing.  Errors: PV_ERR_INVALID_ARG for null
+ * pointers or sizes out of range, PV_ERR_CUDA. */
+#define PV_MLP_HIDDEN 64
+#define PV_MLP_MAX_FEATURES 64
+
+/* Forward pass of `batch` rows of x (batch x F, row-major) into y (batch).
+ * act (batch x 2H: z1 then z2 per row) is written when non-NULL and is what
+ * pv_mlp_backward needs. */
+pv_status pv_mlp_forward(pv_ctx* ctx, const float* params, const float* x, const float* mu, const float* sigma,
+                         int32_t batch, int32_t n_features, float* y, float* act);
+/* Gradient of the mean squared error L = mean((y - target)^2) with respect to
+ * params into grad (overwritten), and L into *loss (device float).  y and act
+ * come from pv_mlp_forward on the same x; dz is caller scratch of
+ * batch x (2H + 1) floats. */
+pv_status pv_mlp_backward(pv_ctx* ctx, const float* params, const float* x, const float* mu, const float* sigma,
+                          const float* act, const float* y, const float* target, int32_t batch,
+                          int32_t n_features, float* dz, float* grad, float* loss);
+/* One Adam step (Kingma and Ba, Algorithm 1) on n parameters in place, with
+ * moment vectors m, v (zero before step 1) and step number step >= 1. */
+pv_status pv_mlp_adam(pv_ctx* ctx, float* params, const float* grad, float* m, float* v, int64_t n, float lr,
+                      float beta1, float beta2, float eps, int32_t step);
+
 /* ---- allocation-free entry point ----------------------------------------- */
 
 /* Largest row count pv_filter_project_noalloc accepts. */

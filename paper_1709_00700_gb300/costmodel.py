@@ -1,0 +1,170 @@
+"""Learned cost model for per-query variant selection.
+
+The paper learns one variant configuration per processor and workload with
+Algorithm 1 and applies it to every query (Section 8.3), and names a
+run-time, per-query optimizer as future work (Section 9.4).  Here a small
+network predicts the log run time of (query, variant) pairs from plan
+features, column statistics and variant features; the pick for a query is
+the variant with the smallest prediction.  Exhaustive search stays the
+fallback and the judge.
+
+Every forward pass, gradient and Adam step runs in libpv's kernels
+(pv_mlp_forward / pv_mlp_backward / pv_mlp_adam); this module holds the
+device buffers and does the bookkeeping.  Training is full batch.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+
+import numpy as np
+
+from . import pv
+
+H = 64
+
+# ---------------------------------------------------------------------------
+# Features
+# ---------------------------------------------------------------------------
+FAMILIES = ("filter", "grouped", "star")
+PLAN_FEATURES = ("log_rows", "sel", "log_sel", "log_groups", "log_groups_per_row", "top_share", "n_preds",
+                 "n_probes", "log_dim_rows", "bytes_in", "bytes_out", "n_aggs", "project", "log_bytes",
+                 "log_out_rows", "fam_filter", "fam_grouped", "fam_star")
+VARIANT_FEATURES = ("multi", "local", "ht_linear", "ht_cuckoo", "ht_perfect", "multshift", "predicated",
+                    "chunked", "log_block", "grid_mult", "unroll", "private_tables", "prefetch", "build_linear",
+                    "build_cuckoo", "build_perfect")
+N_FEATURES = len(PLAN_FEATURES) + len(VARIANT_FEATURES)
+
+
+def plan_vector(st: dict) -> list:
+    """st: rows, sel (estimated fraction of rows surviving filters and
+    probes), groups (estimated distinct groups), top_share (largest group's
+    share of surviving rows), n_preds, n_probes, dim_rows (total build rows),
+    bytes_in / bytes_out per row, n_aggs, project (0/1), family."""
+    rows = max(1.0, float(st["rows"]))
+    sel = min(1.0, max(float(st["sel"]), 1e-6))
+    groups = max(1.0, float(st.get("groups", 1)))
+    fam = st["family"]
+    return [math.log10(rows), sel, math.log10(sel), math.log10(groups), math.log10(groups / rows),
+            float(st.get("top_share", 0.0)), float(st.get("n_preds", 0)), float(st.get("n_probes", 0)),
+            math.log10(1.0 + float(st.get("dim_rows", 0))), float(st.get("bytes_in", 0)),
+            float(st.get("bytes_out", 0)), float(st.get("n_aggs", 0)), float(st.get("project", 0)),
+            math.log10(rows * max(1.0, float(st.get("bytes_in", 1)))), math.log10(1.0 + rows * sel),
+            float(fam == "filter"), float(fam == "grouped"), float(fam == "star")]
+
+
+def variant_vector(v: dict) -> list:
+    ht = v.get("ht", "linear")
+    b = v.get("build", "")
+    return [float(v.get("exec") == "multi"), float(v.get("agg", "local") == "local"), float(ht == "linear"),
+            float(ht == "cuckoo"), float(ht == "perfect"), float(v.get("hash") == "multshift"),
+            float(v.get("pred") == "predicated"), float(v.get("access") == "chunked"),
+            math.log2(v.get("block", 256)), float(v.get("grid_mult", 0)), float(v.get("items_per_thread", 2)),
+            float(v.get("threads_per_table", 0) == 1), float(v.get("prefetch", 0)), float(b == "linear"),
+            float(b == "cuckoo"), float(b == "perfect")]
+
+
+def features(stats: dict, variant: dict) -> np.ndarray:
+    return np.asarray(plan_vector(stats) + variant_vector(variant), dtype=np.float64)
+
+
+# ---------------------------------------------------------------------------
+# Network on the GPU
+# ---------------------------------------------------------------------------
+def n_params(F: int) -> int:
+    return F * H + H + H * H + H + H + 1
+
+
+class Net:
+    """Parameters, Adam moments and standardisation on the device."""
+
+    def __init__(self, ctx: "pv.Context", n_features: int, seed: int = 0):
+        import torch
+        self.torch = torch
+        self.ctx = ctx
+        self.F = n_features
+        rng = np.random.default_rng(seed)
+        F = n_features
+        W1 = rng.uniform(-1, 1, (F, H)) * math.sqrt(6.0 / F)
+        W2 = rng.uniform(-1, 1, (H, H)) * math.sqrt(6.0 / H)
+        w3 = rng.uniform(-1, 1, H) * math.sqrt(6.0 / H)
+        p = np.concatenate([W1.ravel(), np.zeros(H), W2.ravel(), np.zeros(H), w3, np.zeros(1)])
+        dev = f"cuda:{ctx.device}"
+        self.p = torch.tensor(p, dtype=torch.float32, device=dev)
+        self.m = torch.zeros_like(self.p)
+        self.v = torch.zeros_like(self.p)
+        self.g = torch.zeros_like(self.p)
+        self.mu = torch.zeros(F, dtype=torch.float32, device=dev)
+        self.sigma = torch.ones(F, dtype=torch.float32, device=dev)
+        self.step = 0
+
+    @staticmethod
+    def _p(t):
+        return ctypes.c_void_p(t.data_ptr())
+
+    def fit_standardisation(self, X: np.ndarray):
+        X = np.asarray(X, np.float64)
+        sd = X.std(axis=0)
+        sd[sd < 1e-6] = 1.0
+        self.mu.copy_(self.torch.tensor(X.mean(axis=0), dtype=self.torch.float32))
+        self.sigma.copy_(self.torch.tensor(sd, dtype=self.torch.float32))
+
+    def _dev(self, a):
+        return self.torch.tensor(np.asarray(a, np.float32), device=self.p.device)
+
+    def _forward(self, x, B, y, act):
+        lib, ctx = self.ctx.lib, self.ctx
+        ctx._check(lib.pv_mlp_forward(ctx.h, self._p(self.p), self._p(x), self._p(self.mu), self._p(self.sigma), B,
+                                      self.F, self._p(y), self._p(act) if act is not None else None))
+
+    def predict(self, X: np.ndarray) -> np.ndarray:
+        X = np.asarray(X)
+        B = len(X)
+        if B == 0:
+            return np.zeros(0)
+        x = self._dev(X)
+        y = self.torch.empty(B, dtype=self.torch.float32, device=self.p.device)
+        self._forward(x, B, y, None)
+        self.ctx.stream.synchronize()
+        return y.cpu().numpy().astype(np.float64)
+
+    def loss(self, X, t) -> float:
+        y = self.predict(X)
+        return float(np.mean((y - np.asarray(t)) ** 2))
+
+    def train(self, X: np.ndarray, t: np.ndarray, epochs: int = 500, lr: float = 1e-3, batch: int | None = None,
+              report_every: int = 50) -> list:
+        """Full-batch Adam on the mean squared error; returns the loss every
+        report_every epochs."""
+        torch, lib, ctx = self.torch, self.ctx.lib, self.ctx
+        B = len(X)
+        x, tt = self._dev(X), self._dev(t)
+        y = torch.empty(B, dtype=torch.float32, device=self.p.device)
+        act = torch.empty(B * 2 * H, dtype=torch.float32, device=self.p.device)
+        dz = torch.empty(B * (2 * H + 1), dtype=torch.float32, device=self.p.device)
+        loss = torch.empty(1, dtype=torch.float32, device=self.p.device)
+        hist = []
+        n = self.p.numel()
+        for e in range(epochs):
+            self._forward(x, B, y, act)
+            ctx._check(lib.pv_mlp_backward(ctx.h, self._p(self.p), self._p(x), self._p(self.mu), self._p(self.sigma),
+                                           self._p(act), self._p(y), self._p(tt), B, self.F, self._p(dz),
+                                           self._p(self.g), self._p(loss)))
+            self.step += 1
+            ctx._check(lib.pv_mlp_adam(ctx.h, self._p(self.p), self._p(self.g), self._p(self.m), self._p(self.v), n,
+                                       lr, 0.9, 0.999, 1e-8, self.step))
+            if e % report_every == 0 or e == epochs - 1:
+                ctx.stream.synchronize()
+                hist.append(float(loss.item()))
+        return hist
+
+
+# ---------------------------------------------------------------------------
+# Selection
+# ---------------------------------------------------------------------------
+def pick(net: Net, stats: dict, grid: list) -> tuple:
+    """Variant of grid with the smallest predicted log time."""
+    X = np.stack([features(stats, v) for v in grid])
+    pred = net.predict(X)
+    i = int(np.argmin(pred))
+    return grid[i], pred

@@ -1001,6 +1001,32 @@ pv_status pv_kernel_times(pv_ctx* c, float* ms, int32_t max, int32_t* n) {
   return PV_OK;
 }
 
+pv_status pv_mlp_forward(pv_ctx* c, const float* params, const float* x, const float* mu, const float* sigma,
+                         int32_t batch, int32_t n_features, float* y, float* act) {
+  if (!c) return PV_ERR_INVALID_ARG;
+  c->launches = 0;
+  pv_status s = mlp_forward(c->stream, &c->launches, params, x, mu, sigma, batch, n_features, y, act);
+  return s == PV_OK ? s : fail(c, s, "pv_mlp_forward failed");
+}
+
+pv_status pv_mlp_backward(pv_ctx* c, const float* params, const float* x, const float* mu, const float* sigma,
+                          const float* act, const float* y, const float* target, int32_t batch, int32_t n_features,
+                          float* dz, float* grad, float* loss) {
+  if (!c) return PV_ERR_INVALID_ARG;
+  c->launches = 0;
+  pv_status s = mlp_backward(c->stream, &c->launches, params, x, mu, sigma, act, y, target, batch, n_features, dz,
+                             grad, loss);
+  return s == PV_OK ? s : fail(c, s, "pv_mlp_backward failed");
+}
+
+pv_status pv_mlp_adam(pv_ctx* c, float* params, const float* grad, float* m, float* v, int64_t n, float lr,
+                      float beta1, float beta2, float eps, int32_t step) {
+  if (!c) return PV_ERR_INVALID_ARG;
+  c->launches = 0;
+  pv_status s = mlp_adam(c->stream, &c->launches, params, grad, m, v, n, lr, beta1, beta2, eps, step);
+  return s == PV_OK ? s : fail(c, s, "pv_mlp_adam failed");
+}
+
 pv_status pv_debug_spin(pv_ctx* c, int64_t ns) {
   if (!c || ns < 0 || ns > 60ll * 1000 * 1000 * 1000) return PV_ERR_INVALID_ARG;
   k_spin<<<1, 1, 0, c->stream>>>(ns);

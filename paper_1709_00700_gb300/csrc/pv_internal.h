@@ -102,6 +102,15 @@ const ShapeEntry* find_shape(const std::string& sig);
 void register_scan_shapes();
 void register_group_shapes();
 
+// Cost-model kernels (k_mlp.cu).
+pv_status mlp_forward(cudaStream_t s, int* launches, const float* params, const float* x, const float* mu,
+                      const float* sigma, int B, int F, float* y, float* act);
+pv_status mlp_backward(cudaStream_t s, int* launches, const float* params, const float* x, const float* mu,
+                       const float* sigma, const float* act, const float* y, const float* t, int B, int F,
+                       float* dz, float* grad, float* loss);
+pv_status mlp_adam(cudaStream_t s, int* launches, float* p, const float* g, float* m, float* v, int64_t n, float lr,
+                   float b1, float b2, float eps, int step);
+
 // Grid size: grid_mult * SMs, or the number of CTAs resident at once; never
 // more CTAs than there is work for (items_per_cta items each).
 int grid_for(const LaunchCfg& c, const void* kernel, size_t smem, int64_t work_items,

@@ -220,3 +220,56 @@ def star_fact(n: int = 60_000_000, seed: int = DEFAULT_SEED) -> dict:
 def star_schema(n: int = 60_000_000, seed: int = DEFAULT_SEED) -> dict:
     dims = {name: star_dimension(name, rows, g, seed) for name, rows, g in STAR_DIMS}
     return {"fact": star_fact(n, seed), **dims}
+
+
+# ---------------------------------------------------------------------------
+# The same streams computed with torch (on any device), bit-identical to the
+# numpy definitions above.  uint64 arithmetic is carried in int64 tensors:
+# additions and products wrap alike; right shifts are made logical by masking;
+# the unsigned remainder uses u = 2 (u >>> 1) + (u & 1).
+# ---------------------------------------------------------------------------
+def _i64(x: int) -> int:
+    x &= (1 << 64) - 1
+    return x - (1 << 64) if x >= (1 << 63) else x
+
+
+def _shr(z, s: int):
+    import torch
+    return torch.bitwise_and(torch.bitwise_right_shift(z, s), (1 << (64 - s)) - 1)
+
+
+def u64_stream_torch(seed: int, col_id: int, n: int, start: int = 0, device="cpu"):
+    import torch
+    z = torch.arange(start + 1, start + n + 1, dtype=torch.int64, device=device)
+    z.mul_(_i64(int(GOLDEN)))
+    z.add_(_i64(seed_key(seed, col_id)))
+    z.bitwise_xor_(_shr(z, 30))
+    z.mul_(_i64(int(_M1)))
+    z.bitwise_xor_(_shr(z, 27))
+    z.mul_(_i64(int(_M2)))
+    z.bitwise_xor_(_shr(z, 31))
+    return z
+
+
+def uniform_int_torch(seed: int, col_id: int, n: int, lo: int, hi: int, dtype=None, start: int = 0, device="cpu"):
+    import torch
+    span = hi - lo
+    u = u64_stream_torch(seed, col_id, n, start, device)
+    r = torch.remainder(_shr(u, 1), span).mul_(2).add_(torch.bitwise_and(u, 1)).remainder_(span)
+    r.add_(lo)
+    return r.to(dtype or torch.int64)
+
+
+def zipf_keys_torch(seed: int, col_id: int, n: int, g: int, s: float = 1.0, start: int = 0, device="cpu"):
+    import torch
+    w = 1.0 / np.power(np.arange(1, g + 1, dtype=np.float64), s)
+    cdf = np.cumsum(w)
+    cdf /= cdf[-1]
+    u = u64_stream_torch(seed, col_id, n, start, device)
+    p = _shr(u, 11).to(torch.float64).mul_(1.0 / (1 << 53))
+    r = torch.searchsorted(torch.from_numpy(cdf).to(device), p, right=True)
+    r = torch.clamp(r + 1, max=g) - 1
+    a = coprime_multiplier(g)
+    b = (g // 3) if g > 2 else 0
+    k = (r * a + b) % g if g > 1 else torch.zeros_like(r)
+    return k.to(torch.int32)

@@ -114,6 +114,13 @@ _SIGS = {
     "pv_set_kernel_timing": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
     "pv_kernel_times": (ctypes.c_int32, [ctypes.c_void_p, _P(ctypes.c_float), ctypes.c_int32, _P(ctypes.c_int32)]),
     "pv_debug_spin": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int64]),
+    "pv_mlp_forward": (ctypes.c_int32, [ctypes.c_void_p] + [ctypes.c_void_p] * 4 + [ctypes.c_int32, ctypes.c_int32,
+                                                                                    ctypes.c_void_p, ctypes.c_void_p]),
+    "pv_mlp_backward": (ctypes.c_int32, [ctypes.c_void_p] + [ctypes.c_void_p] * 7 + [ctypes.c_int32, ctypes.c_int32]
+                        + [ctypes.c_void_p] * 3),
+    "pv_mlp_adam": (ctypes.c_int32, [ctypes.c_void_p] + [ctypes.c_void_p] * 4 + [ctypes.c_int64, ctypes.c_float,
+                                                                                 ctypes.c_float, ctypes.c_float,
+                                                                                 ctypes.c_float, ctypes.c_int32]),
     "pv_filter_project_noalloc": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                                    ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,

@@ -1,0 +1,335 @@
+"""Variant-selection suite: seeded random queries, exhaustive timing, the
+per-workload configuration of Algorithm 1, and the learned per-query pick.
+
+Three query families shaped like the evaluated pipelines (Section 9.2.1):
+  filter  -- WHERE a < A AND B0 <= b <= B1 -> SUM(price), COUNT(*) or the
+             projection (a, price);
+  grouped -- SUM(val), COUNT(*) WHERE val < T GROUP BY key, G groups,
+             uniform or Zipf(1) keys;
+  star    -- four-probe star join with per-dimension filters, grouped on two
+             dimension attributes.
+Rows are log-uniform in [min_rows, max_rows], the selectivity log-uniform in
+[0.001, 0.9] and the group count log-uniform in [1, 1e7].  The data are
+prefixes of one base table per family generated on the GPU (the grouped
+family's key column is generated per query).
+
+For every query the whole variant grid of its family is timed (exhaustive
+search); the network is trained on the timings of the training queries and
+judged on the held-out ones by t(pick) / t(best).  The same held-out queries
+run under the per-family configuration Algorithm 1 learns from the training
+queries (the method without the network).
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import math
+import time
+
+import numpy as np
+
+from . import autotune, costmodel, datagen, pv, workloads
+
+SAMPLE_ROWS = 65_536
+
+GRIDS = {
+    "filter_aggregate": [dict(pred=p, access=a, items_per_thread=u, block=b, prefetch=f)
+                         for p, a, u, b, f in itertools.product(["branch", "predicated"], ["grid", "chunked"],
+                                                                [1, 4], [256, 512], [0, 1])],
+    "filter_project": [dict(exec=e, pred=p, access=a, items_per_thread=u, block=256, prefetch=f)
+                       for e, p, a, u, f in itertools.product(["single", "multi"], ["branch", "predicated"],
+                                                              ["grid", "chunked"], [1, 4], [0, 1])],
+    "grouped": [dict(s, pred=p, items_per_thread=1, block=256, prefetch=f)
+                for s, p, f in itertools.product(
+                    [dict(agg="local", ht="perfect"), dict(agg="local", ht="perfect", threads_per_table=1),
+                     dict(agg="global", ht="perfect"), dict(agg="local", ht="linear"),
+                     dict(agg="global", ht="linear"), dict(agg="global", ht="linear", exec="multi"),
+                     dict(agg="global", ht="cuckoo", exec="multi"), dict(agg="local", ht="cuckoo", exec="multi")],
+                    ["branch", "predicated"], [0, 1])],
+    "star": [dict(s, build=bk, pred=p, items_per_thread=1, block=512, prefetch=f)
+             for bk, s, p, f in itertools.product(
+                 ["perfect", "linear", "cuckoo"],
+                 [dict(agg="local", ht="perfect"), dict(agg="global", ht="perfect"),
+                  dict(agg="local", ht="linear"), dict(agg="global", ht="linear")],
+                 ["branch", "predicated"], [0, 1])],
+}
+
+
+_DEFAULTS = {"exec": "single", "threads_per_table": 0}
+
+
+def _normalize(grid: list) -> list:
+    """Same keys in every variant of a grid (missing ones take their default)."""
+    keys = []
+    for v in grid:
+        keys += [k for k in v if k not in keys]
+    return [{k: v.get(k, _DEFAULTS.get(k)) for k in keys} for v in grid]
+
+
+GRIDS = {g: _normalize(v) for g, v in GRIDS.items()}
+
+
+def grid_key(q: dict) -> str:
+    if q["family"] == "filter":
+        return "filter_" + q["kind"]
+    return q["family"]
+
+
+def make_queries(n: int = 500, seed: int = 1709, min_rows: int = 1_000_000, max_rows: int = 300_000_000) -> list:
+    rng = np.random.default_rng(seed)
+    qs = []
+    for i in range(n):
+        fam = ("filter", "grouped", "star")[i % 3]
+        rows = int(math.exp(rng.uniform(math.log(min_rows), math.log(max_rows))))
+        rows -= rows % 4
+        sel = math.exp(rng.uniform(math.log(0.001), math.log(0.9)))
+        q = {"id": i, "family": fam, "rows": rows, "sel_target": sel}
+        if fam == "filter":
+            q["kind"] = "aggregate" if rng.random() < 0.5 else "project"
+            # a < A keeps A %, B0 <= b <= B1 keeps (B1 - B0 + 1) %
+            # fraction kept by a, chosen so that b keeps between 1 and 100 percent
+            fa = math.exp(rng.uniform(math.log(max(sel, 0.01)), math.log(min(1.0, 100 * sel))))
+            A = int(np.clip(round(100 * fa), 1, 100))
+            nb = int(np.clip(round(100 * sel / (A / 100)), 1, 100))
+            b0 = int(rng.integers(0, 101 - nb))
+            q.update(A=A, B0=b0, B1=b0 + nb - 1)
+        elif fam == "grouped":
+            G = int(math.exp(rng.uniform(0.0, math.log(1e7))))
+            q.update(G=max(1, G), dist="zipf" if rng.random() < 0.5 else "uniform",
+                     T=int(np.clip(round(sel * 1_000_000), 1, 1_000_000)))
+        else:
+            # per-dimension thresholds whose product is about the target selectivity
+            parts = rng.dirichlet(np.ones(4)) * math.log(sel)
+            q["th"] = {d: int(np.clip(round(100 * math.exp(x)), 1, 100))
+                       for d, x in zip(("d_a", "d_b", "d_c", "d_d"), parts)}
+        qs.append(q)
+    return qs
+
+
+class SuiteData:
+    """Base tables on the device and per-query plans over their prefixes."""
+
+    def __init__(self, ctx: "pv.Context", max_rows: int, seed: int = datagen.DEFAULT_SEED):
+        import torch
+        self.torch = torch
+        self.ctx = ctx
+        dev = f"cuda:{ctx.device}"
+        self.dev = dev
+        self.max_rows = max_rows
+        self.seed = seed
+        u = datagen.uniform_int_torch
+        self.filter = {"a": u(seed, 101, max_rows, 0, 100, torch.int32, device=dev),
+                       "b": u(seed, 102, max_rows, 0, 100, torch.int32, device=dev),
+                       "price": u(seed, 103, max_rows, 100, 10_000_000, torch.int64, device=dev)}
+        self.val = u(seed, 303, max_rows, 0, 1_000_000, torch.int64, device=dev)
+        self.key = torch.empty(max_rows, dtype=torch.int32, device=dev)
+        self.key_of = None
+        self.fact = {"fk_" + name[2:]: u(seed, 501 + j, max_rows, 0, rows, torch.int32, device=dev)
+                     for j, (name, rows, _) in enumerate(datagen.STAR_DIMS)}
+        self.fact["revenue"] = u(seed, 509, max_rows, 100, 10_000_000, torch.int64, device=dev)
+        for name, rows, g in datagen.STAR_DIMS:
+            d = datagen.star_dimension(name, rows, g, seed)
+            ctx.register_table(name, {c: torch.from_numpy(v).to(dev) for c, v in d.items()})
+
+    def _keys(self, q):
+        if self.key_of != (q["G"], q["dist"]):
+            torch = self.torch
+            n = self.max_rows
+            if q["dist"] == "uniform":
+                k = datagen.uniform_int_torch(self.seed, 301, n, 0, q["G"], torch.int32, device=self.dev)
+            else:
+                k = datagen.zipf_keys_torch(self.seed, 302, n, q["G"], device=self.dev)
+            self.key.copy_(k)
+            del k
+            self.key_of = (q["G"], q["dist"])
+        return self.key
+
+    def prepare(self, q: dict, rows: int | None = None) -> dict:
+        """Registers the query's fact table (a prefix of `rows` rows) as
+        table "q" and returns its plan."""
+        r = q["rows"] if rows is None else rows
+        if q["family"] == "filter":
+            self.ctx.register_table("q", {c: t[:r] for c, t in self.filter.items()})
+            plan = {"fact": "q", "filters": [["a", "lt", q["A"]], ["b", "between", q["B0"], q["B1"]]]}
+            if q["kind"] == "aggregate":
+                plan["aggs"] = [["sum", [["x", "price"]]], ["count"]]
+            else:
+                plan["project"] = ["a", "price"]
+            return plan
+        if q["family"] == "grouped":
+            self.ctx.register_table("q", {"key": self._keys(q)[:r], "val": self.val[:r]})
+            return {"fact": "q", "filters": [["val", "lt", q["T"]]], "group_by": ["key"],
+                    "aggs": [["sum", [["x", "val"]]], ["count"]]}
+        self.ctx.register_table("q", {c: t[:r] for c, t in self.fact.items()})
+        plan = workloads.star_plan(q["th"])
+        plan["fact"] = "q"
+        return plan
+
+    def stats(self, q: dict) -> dict:
+        """Plan features and column statistics, from the plan and from
+        pipelines run on the first SAMPLE_ROWS rows (sample selectivity, group
+        count and hottest-group share) through libpv."""
+        ctx = self.ctx
+        n = min(SAMPLE_ROWS, q["rows"])
+        st = {"rows": q["rows"], "family": q["family"], "n_preds": 0, "n_probes": 0, "dim_rows": 0,
+              "n_aggs": 2, "project": 0, "groups": 1, "top_share": 1.0}
+        if q["family"] == "filter":
+            plan = self.prepare(q, n)
+            cnt = int(ctx.query(dict(plan, project=[], aggs=[["sum", [["x", "price"]]], ["count"]]),
+                                pv.variant())[1][0])
+            st.update(sel=max(cnt, 0.5) / n, n_preds=2, bytes_in=16, project=int(q["kind"] == "project"),
+                      bytes_out=12 if q["kind"] == "project" else 0)
+        elif q["family"] == "grouped":
+            plan = self.prepare(q, n)
+            cols = ctx.query(plan, pv.variant(agg="global", ht="linear", items_per_thread=1))
+            counts = cols[2]
+            tot = int(counts.sum())
+            self.prepare(q)
+            lo, hi = ctx.column_stats("q", "key")
+            st.update(sel=max(tot, 0.5) / n, n_preds=1, bytes_in=12, bytes_out=0,
+                      groups=min(hi - lo + 1, q["rows"]), top_share=float(counts.max()) / max(tot, 1))
+        else:
+            plan = self.prepare(q, n)
+            cols = ctx.query(plan, pv.variant(items_per_thread=1, ht="linear"), pv.ht_variant("linear"))
+            counts = cols[3]
+            tot = int(counts.sum())
+            st.update(sel=max(tot, 0.5) / n, n_probes=4, bytes_in=24, bytes_out=0,
+                      dim_rows=sum(r for _, r, _ in datagen.STAR_DIMS), groups=max(len(counts), 1),
+                      top_share=float(counts.max()) / max(tot, 1) if tot else 0.0)
+        return st
+
+
+def time_query(data: SuiteData, q: dict, reps: int = 3) -> dict:
+    """Exhaustive timing of the query's grid; returns {variant key: ms}."""
+    plan = data.prepare(q)
+    grid = GRIDS[grid_key(q)]
+    out = {}
+    if q["family"] == "star":
+        for bk in ("perfect", "linear", "cuckoo"):
+            m = autotune.Measurer(data.ctx, plan, build_ht=bk, reps=reps)
+            for v in grid:
+                if v["build"] == bk:
+                    vv = {k: x for k, x in v.items() if k != "build"}
+                    out[autotune.variant_key(v)] = m(vv)
+            m.close()
+    else:
+        m = autotune.Measurer(data.ctx, plan, reps=reps)
+        for v in grid:
+            out[autotune.variant_key(v)] = m(v)
+        m.close()
+    return out
+
+
+def algorithm1_config(train: list, timings: dict, grid: list, q_sweeps: int = 3) -> dict:
+    """Per-workload configuration (Section 8.3): Algorithm 1 over the grid's
+    dimensions with the workload time = the sum of the training queries'
+    times (looked up from the exhaustive timings; a variant missing from the
+    grid costs infinity)."""
+    names = list(grid[0].keys())
+    dims = []
+    for n in names:
+        vals = []
+        for v in grid:
+            if v[n] not in vals:
+                vals.append(v[n])
+        dims.append((n, vals))
+    keys = {autotune.variant_key(v) for v in grid}
+
+    def cost(v):
+        k = autotune.variant_key(v)
+        if k not in keys:
+            return math.inf
+        return sum(timings[q["id"]].get(k, math.inf) for q in train)
+
+    v, c, n = autotune.feature_wise(cost, dims, q=q_sweeps)
+    return v
+
+
+def run(ctx: "pv.Context", n_queries: int = 500, max_rows: int = 300_000_000, min_rows: int = 1_000_000,
+        n_train: int | None = None, seed: int = 1709, reps: int = 3, epochs: int = 3000, lr: float = 2e-3,
+        log=print) -> dict:
+    t0 = time.time()
+    queries = make_queries(n_queries, seed, min_rows, max_rows)
+    data = SuiteData(ctx, max_rows)
+    stats, timings = {}, {}
+    for i, q in enumerate(queries):
+        stats[q["id"]] = data.stats(q)
+        timings[q["id"]] = time_query(data, q, reps)
+        if log and (i % 25 == 0 or i == len(queries) - 1):
+            log(f"  timed {i + 1}/{len(queries)} queries, {time.time() - t0:.0f}s")
+    t_explore = time.time() - t0
+    rng = np.random.default_rng(seed + 1)
+    order = rng.permutation(len(queries))
+    n_train = n_train if n_train is not None else int(round(0.8 * len(queries)))
+    train = [queries[i] for i in order[:n_train]]
+    test = [queries[i] for i in order[n_train:]]
+
+    def rows_of(qs):
+        X, y = [], []
+        for q in qs:
+            for v in GRIDS[grid_key(q)]:
+                ms = timings[q["id"]][autotune.variant_key(v)]
+                if math.isfinite(ms):
+                    X.append(costmodel.features(stats[q["id"]], v))
+                    y.append(math.log(ms))
+        return np.array(X), np.array(y)
+
+    X, y = rows_of(train)
+    t1 = time.time()
+    net = costmodel.Net(ctx, costmodel.N_FEATURES, seed=seed)
+    net.fit_standardisation(X)
+    hist = net.train(X, y, epochs=epochs, lr=lr, report_every=max(1, epochs // 10))
+    t_train = time.time() - t1
+    configs = {g: algorithm1_config([q for q in train if grid_key(q) == g], timings, GRIDS[g]) for g in GRIDS}
+    per_query = []
+    for q in test:
+        grid = GRIDS[grid_key(q)]
+        tm = timings[q["id"]]
+        finite = [v for v in grid if math.isfinite(tm[autotune.variant_key(v)])]
+        best = min(tm[autotune.variant_key(v)] for v in finite)
+        pick, _ = costmodel.pick(net, stats[q["id"]], finite)
+        t_pick = tm[autotune.variant_key(pick)]
+        cfg = configs[grid_key(q)]
+        t_cfg = tm.get(autotune.variant_key(cfg), math.inf)
+        per_query.append({"id": q["id"], "family": grid_key(q), "rows": q["rows"], "best_ms": best,
+                          "pick_ms": t_pick, "config_ms": t_cfg, "pick": pick})
+    r_pick = np.array([p["pick_ms"] / p["best_ms"] for p in per_query])
+    r_cfg = np.array([p["config_ms"] / p["best_ms"] for p in per_query])
+    summary = {
+        "queries": len(queries), "train": len(train), "held_out": len(test),
+        "grid_sizes": {g: len(v) for g, v in GRIDS.items()},
+        "exploration_s": t_explore, "train_s": t_train, "train_rows": len(X), "loss_history": hist,
+        "mlp_within_10pct": float(np.mean(r_pick <= 1.10)),
+        "mlp_geomean_slowdown": float(np.exp(np.mean(np.log(r_pick)))),
+        "mlp_worst_slowdown": float(r_pick.max()),
+        "alg1_within_10pct": float(np.mean(r_cfg <= 1.10)),
+        "alg1_geomean_slowdown": float(np.exp(np.mean(np.log(np.minimum(r_cfg, 1e6))))),
+        "alg1_worst_slowdown": float(r_cfg.max()),
+        "alg1_configs": configs,
+        "per_query": per_query,
+    }
+    return summary
+
+
+def main(argv=None):
+    import argparse
+    ap = argparse.ArgumentParser(description="variant-selection suite on one GPU")
+    ap.add_argument("--queries", type=int, default=500)
+    ap.add_argument("--max-rows", type=int, default=300_000_000)
+    ap.add_argument("--min-rows", type=int, default=1_000_000)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--epochs", type=int, default=3000)
+    ap.add_argument("--out", default="")
+    a = ap.parse_args(argv)
+    ctx = pv.Context(0)
+    summary = run(ctx, a.queries, a.max_rows, a.min_rows, reps=a.reps, epochs=a.epochs)
+    brief = {k: v for k, v in summary.items() if k != "per_query"}
+    print(json.dumps(brief))
+    if a.out:
+        with open(a.out, "w") as f:
+            json.dump(summary, f)
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,24 @@
+"""A small variant-selection suite end to end on the GPU: random queries of
+the three families, exhaustive timing, Algorithm 1 per family, and the cost
+model trained with its own kernels and judged on held-out queries."""
+import math
+
+import pytest
+
+from paper_1709_00700_gb300 import autotune, pv, suite
+
+pytestmark = pytest.mark.gpu
+
+
+def test_small_suite_runs_and_picks_from_the_grid():
+    ctx = pv.Context(0)
+    s = suite.run(ctx, n_queries=24, max_rows=2_000_000, min_rows=200_000, reps=2, epochs=300, log=None)
+    ctx.close()
+    assert s["held_out"] == 5 and s["train"] == 19
+    assert s["loss_history"][-1] < s["loss_history"][0]
+    for p in s["per_query"]:
+        grid = [autotune.variant_key(v) for v in suite.GRIDS[p["family"]]]
+        assert autotune.variant_key(p["pick"]) in grid
+        assert p["best_ms"] <= p["pick_ms"] and p["best_ms"] <= p["config_ms"]
+        assert math.isfinite(p["pick_ms"])
+    assert 0.0 <= s["mlp_within_10pct"] <= 1.0
