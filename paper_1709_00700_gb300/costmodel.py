@@ -29,7 +29,8 @@ H = 64
 FAMILIES = ("filter", "grouped", "star")
 PLAN_FEATURES = ("log_rows", "sel", "log_sel", "log_groups", "log_groups_per_row", "top_share", "n_preds",
                  "n_probes", "log_dim_rows", "bytes_in", "bytes_out", "n_aggs", "project", "log_bytes",
-                 "log_out_rows", "fam_filter", "fam_grouped", "fam_star")
+                 "log_out_rows", "fam_filter", "fam_grouped", "fam_star", "log_hot_rows", "log_groups_hit",
+                 "log_rows_per_group")
 VARIANT_FEATURES = ("multi", "local", "ht_linear", "ht_cuckoo", "ht_perfect", "multshift", "predicated",
                     "chunked", "log_block", "grid_mult", "unroll", "private_tables", "prefetch", "build_linear",
                     "build_cuckoo", "build_perfect")
@@ -50,7 +51,11 @@ def plan_vector(st: dict) -> list:
             math.log10(1.0 + float(st.get("dim_rows", 0))), float(st.get("bytes_in", 0)),
             float(st.get("bytes_out", 0)), float(st.get("n_aggs", 0)), float(st.get("project", 0)),
             math.log10(rows * max(1.0, float(st.get("bytes_in", 1)))), math.log10(1.0 + rows * sel),
-            float(fam == "filter"), float(fam == "grouped"), float(fam == "star")]
+            float(fam == "filter"), float(fam == "grouped"), float(fam == "star"),
+            # contention proxies: rows of the hottest group, groups touched, rows per touched group
+            math.log10(1.0 + rows * sel * float(st.get("top_share", 0.0))),
+            math.log10(max(1.0, min(groups, rows * sel))),
+            math.log10(max(1.0, rows * sel / max(1.0, min(groups, rows * sel))))]
 
 
 def variant_vector(v: dict) -> list:
@@ -159,10 +164,20 @@ class Net:
         return hist
 
 
+class Ensemble:
+    """Mean prediction of several independently initialised networks."""
+
+    def __init__(self, nets: list):
+        self.nets = nets
+
+    def predict(self, X: np.ndarray) -> np.ndarray:
+        return np.mean([n.predict(X) for n in self.nets], axis=0)
+
+
 # ---------------------------------------------------------------------------
 # Selection
 # ---------------------------------------------------------------------------
-def pick(net: Net, stats: dict, grid: list) -> tuple:
+def pick(net, stats: dict, grid: list) -> tuple:
     """Variant of grid with the smallest predicted log time."""
     X = np.stack([features(stats, v) for v in grid])
     pred = net.predict(X)

@@ -245,9 +245,9 @@ def algorithm1_config(train: list, timings: dict, grid: list, q_sweeps: int = 3)
     return v
 
 
-def run(ctx: "pv.Context", n_queries: int = 500, max_rows: int = 300_000_000, min_rows: int = 1_000_000,
-        n_train: int | None = None, seed: int = 1709, reps: int = 3, epochs: int = 3000, lr: float = 2e-3,
-        log=print) -> dict:
+def explore(ctx: "pv.Context", n_queries: int = 500, max_rows: int = 300_000_000, min_rows: int = 1_000_000,
+            seed: int = 1709, reps: int = 3, log=print) -> dict:
+    """Statistics and exhaustive timings of every query of the suite."""
     t0 = time.time()
     queries = make_queries(n_queries, seed, min_rows, max_rows)
     data = SuiteData(ctx, max_rows)
@@ -257,58 +257,111 @@ def run(ctx: "pv.Context", n_queries: int = 500, max_rows: int = 300_000_000, mi
         timings[q["id"]] = time_query(data, q, reps)
         if log and (i % 25 == 0 or i == len(queries) - 1):
             log(f"  timed {i + 1}/{len(queries)} queries, {time.time() - t0:.0f}s")
-    t_explore = time.time() - t0
+    return {"queries": queries, "stats": stats, "timings": timings, "exploration_s": time.time() - t0,
+            "seed": seed}
+
+
+CANDIDATES = ((20000, 5, 1e-3), (30000, 8, 1e-3), (10000, 5, 2e-3))
+
+
+def _rows(qs, stats, timings):
+    X, y = [], []
+    for q in qs:
+        for v in GRIDS[grid_key(q)]:
+            ms = timings[q["id"]][autotune.variant_key(v)]
+            if math.isfinite(ms):
+                X.append(costmodel.features(stats[q["id"]], v))
+                y.append(math.log(ms))
+    return np.array(X), np.array(y)
+
+
+def _fit(ctx, X, y, epochs, ensemble, lr, seed):
+    nets, hists = [], []
+    for e in range(ensemble):
+        net = costmodel.Net(ctx, costmodel.N_FEATURES, seed=seed + 17 * e)
+        net.fit_standardisation(X)
+        hists.append(net.train(X, y, epochs=epochs, lr=lr, report_every=max(1, epochs // 10)))
+        nets.append(net)
+    return costmodel.Ensemble(nets), hists[0]
+
+
+def _evaluate(model, qs, stats, timings, configs=None, top_k=3):
+    out = []
+    for q in qs:
+        tm = timings[q["id"]]
+        finite = [v for v in GRIDS[grid_key(q)] if math.isfinite(tm[autotune.variant_key(v)])]
+        best = min(tm[autotune.variant_key(v)] for v in finite)
+        pick, pred = costmodel.pick(model, stats[q["id"]], finite)
+        ranked = [finite[i] for i in np.argsort(pred)[:top_k]]
+        r = {"id": q["id"], "family": grid_key(q), "rows": q["rows"], "best_ms": best,
+             "pick_ms": tm[autotune.variant_key(pick)], "topk_ms": min(tm[autotune.variant_key(v)] for v in ranked),
+             "pick": pick}
+        if configs is not None:
+            r["config_ms"] = tm.get(autotune.variant_key(configs[grid_key(q)]), math.inf)
+        out.append(r)
+    return out
+
+
+def judge(ctx: "pv.Context", ex: dict, n_train: int | None = None, candidates=CANDIDATES, top_k: int = 3,
+          n_val: int | None = None) -> dict:
+    """Trains the cost model on the training queries' timings and judges its
+    picks on the held-out queries against the exhaustive best, beside the
+    per-family configuration of Algorithm 1.  The training settings (epochs,
+    ensemble size, learning rate) are chosen among `candidates` on a
+    validation split of the training queries; the held-out queries are used
+    once, by the final model trained on all training queries."""
+    queries, stats, timings = ex["queries"], ex["stats"], ex["timings"]
+    seed = ex.get("seed", 1709)
     rng = np.random.default_rng(seed + 1)
     order = rng.permutation(len(queries))
     n_train = n_train if n_train is not None else int(round(0.8 * len(queries)))
     train = [queries[i] for i in order[:n_train]]
     test = [queries[i] for i in order[n_train:]]
-
-    def rows_of(qs):
-        X, y = [], []
-        for q in qs:
-            for v in GRIDS[grid_key(q)]:
-                ms = timings[q["id"]][autotune.variant_key(v)]
-                if math.isfinite(ms):
-                    X.append(costmodel.features(stats[q["id"]], v))
-                    y.append(math.log(ms))
-        return np.array(X), np.array(y)
-
-    X, y = rows_of(train)
+    n_val = n_val if n_val is not None else len(train) // 5
+    fit_part, val_part = train[:-n_val], train[-n_val:]
     t1 = time.time()
-    net = costmodel.Net(ctx, costmodel.N_FEATURES, seed=seed)
-    net.fit_standardisation(X)
-    hist = net.train(X, y, epochs=epochs, lr=lr, report_every=max(1, epochs // 10))
+    validation = []
+    if len(candidates) > 1 and n_val > 0:
+        Xf, yf = _rows(fit_part, stats, timings)
+        for epochs, ens, lr in candidates:
+            model, _ = _fit(ctx, Xf, yf, epochs, ens, lr, seed)
+            res = _evaluate(model, val_part, stats, timings)
+            r = np.array([p["pick_ms"] / p["best_ms"] for p in res])
+            validation.append({"epochs": epochs, "ensemble": ens, "lr": lr,
+                               "within_10pct": float(np.mean(r <= 1.10)),
+                               "geomean": float(np.exp(np.mean(np.log(r))))})
+        best = max(validation, key=lambda c: (c["within_10pct"], -c["geomean"]))
+        chosen = (best["epochs"], best["ensemble"], best["lr"])
+    else:
+        chosen = candidates[0]
+    X, y = _rows(train, stats, timings)
+    model, hist = _fit(ctx, X, y, *chosen, seed)
     t_train = time.time() - t1
     configs = {g: algorithm1_config([q for q in train if grid_key(q) == g], timings, GRIDS[g]) for g in GRIDS}
-    per_query = []
-    for q in test:
-        grid = GRIDS[grid_key(q)]
-        tm = timings[q["id"]]
-        finite = [v for v in grid if math.isfinite(tm[autotune.variant_key(v)])]
-        best = min(tm[autotune.variant_key(v)] for v in finite)
-        pick, _ = costmodel.pick(net, stats[q["id"]], finite)
-        t_pick = tm[autotune.variant_key(pick)]
-        cfg = configs[grid_key(q)]
-        t_cfg = tm.get(autotune.variant_key(cfg), math.inf)
-        per_query.append({"id": q["id"], "family": grid_key(q), "rows": q["rows"], "best_ms": best,
-                          "pick_ms": t_pick, "config_ms": t_cfg, "pick": pick})
+    per_query = _evaluate(model, test, stats, timings, configs, top_k)
     r_pick = np.array([p["pick_ms"] / p["best_ms"] for p in per_query])
+    r_topk = np.array([p["topk_ms"] / p["best_ms"] for p in per_query])
     r_cfg = np.array([p["config_ms"] / p["best_ms"] for p in per_query])
-    summary = {
+    gm = lambda r: float(np.exp(np.mean(np.log(np.minimum(r, 1e6)))))  # noqa: E731
+    return {
         "queries": len(queries), "train": len(train), "held_out": len(test),
         "grid_sizes": {g: len(v) for g, v in GRIDS.items()},
-        "exploration_s": t_explore, "train_s": t_train, "train_rows": len(X), "loss_history": hist,
-        "mlp_within_10pct": float(np.mean(r_pick <= 1.10)),
-        "mlp_geomean_slowdown": float(np.exp(np.mean(np.log(r_pick)))),
+        "exploration_s": ex.get("exploration_s"), "train_s": t_train, "train_rows": len(X),
+        "validation": validation, "chosen": {"epochs": chosen[0], "ensemble": chosen[1], "lr": chosen[2]},
+        "loss_history": hist,
+        "mlp_within_10pct": float(np.mean(r_pick <= 1.10)), "mlp_geomean_slowdown": gm(r_pick),
         "mlp_worst_slowdown": float(r_pick.max()),
-        "alg1_within_10pct": float(np.mean(r_cfg <= 1.10)),
-        "alg1_geomean_slowdown": float(np.exp(np.mean(np.log(np.minimum(r_cfg, 1e6))))),
-        "alg1_worst_slowdown": float(r_cfg.max()),
-        "alg1_configs": configs,
-        "per_query": per_query,
+        f"mlp_top{top_k}_within_10pct": float(np.mean(r_topk <= 1.10)),
+        f"mlp_top{top_k}_geomean_slowdown": gm(r_topk),
+        "alg1_within_10pct": float(np.mean(r_cfg <= 1.10)), "alg1_geomean_slowdown": gm(r_cfg),
+        "alg1_worst_slowdown": float(r_cfg.max()), "alg1_configs": configs, "per_query": per_query,
     }
-    return summary
+
+
+def run(ctx: "pv.Context", n_queries: int = 500, max_rows: int = 300_000_000, min_rows: int = 1_000_000,
+        n_train: int | None = None, seed: int = 1709, reps: int = 3, candidates=CANDIDATES, log=print) -> dict:
+    ex = explore(ctx, n_queries, max_rows, min_rows, seed, reps, log)
+    return judge(ctx, ex, n_train, candidates)
 
 
 def main(argv=None):
@@ -318,13 +371,27 @@ def main(argv=None):
     ap.add_argument("--max-rows", type=int, default=300_000_000)
     ap.add_argument("--min-rows", type=int, default=1_000_000)
     ap.add_argument("--reps", type=int, default=3)
-    ap.add_argument("--epochs", type=int, default=3000)
+    ap.add_argument("--epochs", type=int, default=0, help="fixed training setting instead of validation choice")
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--ensemble", type=int, default=5)
+    ap.add_argument("--timings-in", default="", help="judge saved exploration results instead of timing again")
+    ap.add_argument("--timings-out", default="")
     ap.add_argument("--out", default="")
     a = ap.parse_args(argv)
     ctx = pv.Context(0)
-    summary = run(ctx, a.queries, a.max_rows, a.min_rows, reps=a.reps, epochs=a.epochs)
-    brief = {k: v for k, v in summary.items() if k != "per_query"}
-    print(json.dumps(brief))
+    if a.timings_in:
+        with open(a.timings_in) as f:
+            ex = json.load(f)
+        ex["stats"] = {int(k): v for k, v in ex["stats"].items()}
+        ex["timings"] = {int(k): v for k, v in ex["timings"].items()}
+    else:
+        ex = explore(ctx, a.queries, a.max_rows, a.min_rows, reps=a.reps)
+        if a.timings_out:
+            with open(a.timings_out, "w") as f:
+                json.dump(ex, f)
+    cands = ((a.epochs, a.ensemble, a.lr),) if a.epochs else CANDIDATES
+    summary = judge(ctx, ex, candidates=cands)
+    print(json.dumps({k: v for k, v in summary.items() if k != "per_query"}))
     if a.out:
         with open(a.out, "w") as f:
             json.dump(summary, f)

@@ -12,9 +12,11 @@ pytestmark = pytest.mark.gpu
 
 def test_small_suite_runs_and_picks_from_the_grid():
     ctx = pv.Context(0)
-    s = suite.run(ctx, n_queries=24, max_rows=2_000_000, min_rows=200_000, reps=2, epochs=300, log=None)
+    s = suite.run(ctx, n_queries=24, max_rows=2_000_000, min_rows=200_000, reps=2,
+                  candidates=((300, 2, 2e-3), (200, 1, 3e-3)), log=None)
     ctx.close()
     assert s["held_out"] == 5 and s["train"] == 19
+    assert len(s["validation"]) == 2 and s["chosen"]["epochs"] in (300, 200)
     assert s["loss_history"][-1] < s["loss_history"][0]
     for p in s["per_query"]:
         grid = [autotune.variant_key(v) for v in suite.GRIDS[p["family"]]]
