@@ -77,6 +77,31 @@ def make_tables(name: str, rows: int, groups: int):
     raise ValueError(name)
 
 
+TUNE_GRID = {"lowcard": "grouped", "keyval": "grouped", "filter_agg": "filter_aggregate",
+             "filter_project": "filter_project", "star": "star"}
+
+
+def tune(ctx, plan, name, reps=3):
+    """Exhaustive search over the workload's variant grid (the grids of the
+    variant-selection suite); returns (best variant, its ms, grid size, s)."""
+    from paper_1709_00700_gb300 import autotune, suite
+    grid = suite.GRIDS[TUNE_GRID[name]]
+    t0 = time.perf_counter()
+    best, best_ms = None, float("inf")
+    builds = sorted({v.get("build", "") for v in grid})
+    for bk in builds:
+        m = autotune.Measurer(ctx, plan, build_ht=bk or "perfect", reps=reps)
+        for v in grid:
+            if v.get("build", "") != bk:
+                continue
+            vv = {k: x for k, x in v.items() if k != "build"}
+            ms = m(vv)
+            if ms < best_ms:
+                best, best_ms = dict(v), ms
+        m.close()
+    return best, best_ms, len(grid), time.perf_counter() - t0
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -324,16 +349,22 @@ def run_pv(args):
     w = WORKLOADS[args.workload]
     rows = args.rows or w["rows"]
     tables, plan = make_tables(args.workload, rows, args.groups)
-    var_kw = dict(TUNED[args.workload])
-    if args.variant:
-        var_kw.update(json.loads(args.variant))
-    var = pv.variant(**var_kw)
     ctx = pv.Context(local)
     dev = {t: {c: torch.from_numpy(np.ascontiguousarray(v)).cuda(local) for c, v in cols.items()}
            for t, cols in tables.items()}
     for t, cols in dev.items():
         ctx.register_table(t, cols)
-    hts = ctx.build_all(plan, pv.ht_variant(args.build_ht))
+    tuning = None
+    if args.variant:
+        var_kw = json.loads(args.variant)
+    elif args.no_tune:
+        var_kw = dict(TUNED[args.workload])
+    else:
+        var_kw, ms, n, secs = tune(ctx, plan, args.workload)
+        tuning = {"grid": TUNE_GRID[args.workload], "variants": n, "best_ms": ms, "seconds": secs}
+    build_ht = var_kw.pop("build", None) or args.build_ht
+    var = pv.variant(**var_kw)
+    hts = ctx.build_all(plan, pv.ht_variant(build_ht))
     res = ctx.run(plan, var, hts)
     ctx.sync()
     first = [c.astype(np.int64) for c in ctx.fetch(res)]
@@ -342,7 +373,6 @@ def run_pv(args):
         passing = int((tables["li"]["date"] <= workloads.LOWCARD_DAY_HI).sum())
         assert int(first[nk + 7].sum()) == passing, "count invariant failed"
     stream = ctx.stream
-    ctx.set_kernel_timing(True)
     clk = ClockSampler(local).start()
     clk.t_load = time.time()
     for _ in range(max(args.warmup, 1)):
@@ -351,7 +381,6 @@ def run_pv(args):
     ctx.sync()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    kernel_ms = []
     launches_per_step = 0
     barrier(dist)
     torch.cuda.synchronize()
@@ -368,13 +397,21 @@ def run_pv(args):
         ctx.rerun(res)
         ends[i].record(stream)
         launches_per_step = ctx.last_launch_count()
-        kernel_ms.append(ctx.kernel_times())
     torch.cuda.synchronize()
     clk.t1 = time.time()
     if nv:
         nv.__exit__()
     clk.stop()
     barrier(dist)
+    # per-kernel durations, measured on separate steps: with kernel timing on,
+    # the library brackets every kernel with events and launches them apart
+    ctx.set_kernel_timing(True)
+    kernel_ms = []
+    for i in range(max(3, min(args.steps, 20))):
+        ctx.lib.pv_l2_flush(ctx.h)
+        ctx.rerun(res)
+        kernel_ms.append(ctx.kernel_times())
+    ctx.set_kernel_timing(False)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_s = max_over_ranks(dist, sum(step_ms) / 1000.0)
     value = rows * world * args.steps / total_s
@@ -390,7 +427,6 @@ def run_pv(args):
     pinned = {t: {c: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for c, v in cols.items()}
               for t, cols in tables.items()}
     h2d = sum(v.numel() * v.element_size() for cols in pinned.values() for v in cols.values())
-    ctx.set_kernel_timing(False)
     e2e_steps = max(3, min(args.steps, 10))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -409,7 +445,8 @@ def run_pv(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000 * total_s / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic (seeded counter-based generator)",
-        "config": {"workload": w["desc"], "rows": rows, "variant": var_kw,
+        "config": {"workload": w["desc"], "rows": rows, "variant": dict(var_kw, build=build_ht),
+                   "tuning": tuning,
                    "l2": "flushed (2x L2 write) before every step, outside the timed events",
                    "seed": datagen.DEFAULT_SEED, "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -442,7 +479,8 @@ def main():
     ap.add_argument("--workload", default="lowcard", choices=sorted(WORKLOADS))
     ap.add_argument("--rows", type=int, default=0)
     ap.add_argument("--groups", type=int, default=1000)
-    ap.add_argument("--variant", default="", help="JSON overrides of the pv_variant fields")
+    ap.add_argument("--variant", default="", help="JSON pv_variant fields (skips tuning)")
+    ap.add_argument("--no-tune", action="store_true", help="use the built-in variant instead of tuning")
     ap.add_argument("--build-ht", default="perfect")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -400,6 +400,72 @@ struct SinkLocalHash {
   }
 };
 
+// Extraction: a warp-uniform sweep (thread t of T) over the cap + 1 slots;
+// non-empty slots are appended to the dense result columns with one atomicAdd
+// per warp, then emptied.  Slot words are read from L2: they were written by
+// atomics of other CTAs.
+__device__ __forceinline__ int64_t decode_agg(int func, uint64_t c) {
+  if (func == PV_MIN) return decode_min(c);
+  if (func == PV_MAX) return decode_max(c);
+  return static_cast<int64_t>(c);
+}
+
+__device__ __forceinline__ void extract_slots(const GroupDesc& gd, const GroupOut& g, int64_t t, int64_t T) {
+  const int64_t total = g.cap + 1;
+  const int lane = threadIdx.x & 31;
+  const bool perfect = g.ht == PV_HT_PERFECT;
+  const int na = gd.n_aggs;
+  for (int64_t wb = t - lane; wb < total; wb += T) {
+    const int64_t s = wb + lane;
+    bool occ = false, dirty = false;
+    uint64_t key = kEmpty64;
+    unsigned long long* v = g.vals + s * g.stride;
+    if (s < total) {
+      if (perfect) {
+        occ = s < g.cap && __ldcg(v + gd.count_word) != 0;
+        dirty = occ;
+      } else if (s < g.cap) {
+        key = __ldcg(g.keys + s);
+        dirty = key != kEmpty64;
+        occ = dirty && __ldcg(v + gd.count_word) != 0;
+      } else {
+        occ = dirty = __ldcg(v + gd.count_word) != 0;
+      }
+    }
+    const unsigned ball = __ballot_sync(0xffffffffu, occ);
+    unsigned long long base = 0;
+    if (lane == 0 && ball) base = atomicAdd(g.out_count, static_cast<unsigned long long>(__popc(ball)));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (occ) {
+      const int64_t pos = static_cast<int64_t>(base) + __popc(ball & ((1u << lane) - 1u));
+      if (pos < g.out_cap) {
+        int64_t k0, k1 = 0;
+        if (perfect) {
+          if (gd.n_keys == 1) {
+            k0 = gd.key_min[0] + s;
+          } else {
+            k0 = gd.key_min[0] + s / gd.key_span[1];
+            k1 = gd.key_min[1] + s % gd.key_span[1];
+          }
+        } else if (gd.n_keys == 1) {
+          k0 = gd.key64[0] ? static_cast<int64_t>(key) : static_cast<int64_t>(static_cast<int32_t>(static_cast<uint32_t>(key)));
+        } else {
+          k0 = static_cast<int32_t>(static_cast<uint32_t>(key >> 32));
+          k1 = static_cast<int32_t>(static_cast<uint32_t>(key));
+        }
+        g.out[pos] = k0;
+        if (gd.n_keys == 2) g.out[g.out_cap + pos] = k1;
+        for (int a = 0; a < na; ++a) g.out[(gd.n_keys + a) * g.out_cap + pos] = decode_agg(gd.func[a], __ldcg(v + a));
+      }
+    }
+    if (dirty) {
+      for (int a = 0; a <= na; ++a) v[a] = 0;
+      if (!perfect && s < g.cap) g.keys[s] = kEmpty64;
+    }
+  }
+}
+
+
 // ---------------------------------------------------------------------------
 // Kernels
 // ---------------------------------------------------------------------------
@@ -423,12 +489,13 @@ __global__ void __maxnreg__(128) k_group(const __grid_constant__ KParams kp, con
   if constexpr (PRED) {
     for_items_pipelined<SH, CHUNK, U>(kp, consume);
   } else {
-    for_items_pf<SH, CHUNK, U>(kp, [&](const int64_t (&idx)[U]) {
+    for_items<CHUNK, U>(kp.n_items, [&](const int64_t (&idx)[U]) {
       Item<SH> it[U];
       eval_items<SH, PRED, U>(it, kp, idx);
       consume(it);
     });
   }
+  pdl_launch_dependents();  // the extraction kernel may start launching now
   sink.finish();
 }
 

@@ -244,10 +244,12 @@ __global__ void __maxnreg__(128) k_project_count(const __grid_constant__ KParams
     block_excl_scan(cnt, &total);
     if (threadIdx.x == 0) out.tile_count[tile] = static_cast<int64_t>(total);
   });
+  pdl_launch_dependents();
 }
 
 // Exclusive prefix sum over the tile counts (one CTA of 1024 threads).
 __global__ void __launch_bounds__(1024) k_tile_scan(const __grid_constant__ ProjOut out, int32_t* err) {
+  pdl_wait();  // launched early behind the count kernel
   const int64_t n = out.n_tiles;
   const int64_t per = (n + blockDim.x - 1) / blockDim.x;
   const int64_t b = threadIdx.x * per;
@@ -260,6 +262,7 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const __grid_constant__ Proj
     out.tile_offset[i] = static_cast<int64_t>(run);
     run += out.tile_count[i];
   }
+  pdl_launch_dependents();
   if (threadIdx.x == 0) {
     const int64_t t = static_cast<int64_t>(total);
     *out.count = t < out.capacity ? t : out.capacity;
@@ -270,6 +273,7 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const __grid_constant__ Proj
 template <class SH, bool PRED, bool CHUNK, int U>
 __global__ void __maxnreg__(128) k_project_scatter(const __grid_constant__ KParams kp, const __grid_constant__ ProjOut out) {
   static_assert(U <= 4, "16-bit scan fields hold at most 4 unroll slots");
+  pdl_wait();  // launched early behind the scan kernel
   for_tiles<CHUNK>(out.n_tiles, [&](int64_t tile) {
     int64_t idx[U];
     tile_items<CHUNK, U>(tile, idx);
@@ -349,12 +353,15 @@ static pv_status launch_proj_t(const LaunchCfg& c, const KParams& kp, const Proj
     kc<<<grid, c.block, 0, c.stream>>>(kp, out);
     kmark(c);
     kmark(c);
-    k_tile_scan<<<1, 1024, 0, c.stream>>>(out, kp.err);
+    cudaError_t e1 = c.mark ? (k_tile_scan<<<1, 1024, 0, c.stream>>>(out, kp.err), cudaSuccess)
+                            : pdl_launch(k_tile_scan, dim3(1), dim3(1024), 0, c.stream, out, kp.err);
     kmark(c);
     kmark(c);
-    ks<<<grid, c.block, 0, c.stream>>>(kp, out);
+    cudaError_t e2 = c.mark ? (ks<<<grid, c.block, 0, c.stream>>>(kp, out), cudaSuccess)
+                            : pdl_launch(ks, dim3(grid), dim3(c.block), 0, c.stream, kp, out);
     kmark(c);
     *c.launches += 3;
+    if (e1 != cudaSuccess || e2 != cudaSuccess) return PV_ERR_CUDA;
   }
   return cudaGetLastError() == cudaSuccess ? PV_OK : PV_ERR_CUDA;
 }

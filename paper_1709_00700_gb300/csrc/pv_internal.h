@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <string>
+#include <utility>
 #include <vector>
 #include <cuda_runtime.h>
 
@@ -29,6 +30,31 @@ struct LaunchCfg {
   void (*mark)(void* timer, cudaStream_t s);
   void* timer;
 };
+
+// Programmatic dependent launch (sm_90+): a kernel launched with
+// pdl_launch() may start while its predecessor on the stream finishes; it
+// must call pdl_wait() before touching anything the predecessor wrote
+// (griddepcontrol.wait returns once the predecessor grid has completed and
+// its memory is visible).  pdl_launch_dependents() lets the dependent grid
+// be scheduled before this grid ends.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
+template <class... KArgs, class... Args>
+inline cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 inline void kmark(const LaunchCfg& c) {
   if (c.mark) c.mark(c.timer, c.stream);
