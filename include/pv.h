@@ -236,7 +236,9 @@ pv_status pv_graph_launch(pv_ctx* ctx, pv_graph g);
 
 /* ---- measurement support ------------------------------------------------ */
 
-/* Overwrites a ctx-owned buffer of twice the L2 size (cold-cache timing). */
+/* Cold-cache timing: overwrites a ctx-owned buffer of twice the L2 size (evicting
+ * every other line), then discards that buffer's lines from L2 without write-back,
+ * leaving L2 cold and clean. */
 pv_status pv_l2_flush(pv_ctx* ctx);
 /* Kernels enqueued by the last pv_run_pipeline / pv_rerun / pv_build_hash_table. */
 pv_status pv_last_launch_count(pv_ctx* ctx, int32_t* n);

@@ -1,0 +1,109 @@
+"""Parity at the configurations' full sizes, in the launch configuration the
+benchmark times (its tuned variants) and in others: every result compared
+exactly with the oracle (threaded over the host cores).  Large tables are
+generated on the GPU with the generator bit-identical to the numpy one and
+copied to the host for the oracle."""
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_1709_00700_gb300 import datagen, pv, workloads
+from tests.gpu_util import assert_same
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = pv.Context(0)
+    yield c
+    c.close()
+
+
+def _oracle(plan, tables):
+    return oracle.run(plan, tables, nthreads=oracle.hardware_threads())["cols"]
+
+
+def _register_host(ctx, tables):
+    import torch
+    for t, cols in tables.items():
+        ctx.register_table(t, {c: torch.from_numpy(np.ascontiguousarray(v)).cuda() for c, v in cols.items()})
+
+
+def test_filter_queries_1m_rows(ctx):
+    t = {"t": datagen.table_filter_agg(1_000_000)}
+    _register_host(ctx, t)
+    plan = workloads.filter_agg_plan()
+    w = _oracle(plan, t)
+    for kw in (dict(pred="branch", access="chunked", items_per_thread=4, block=512, prefetch=1),
+               dict(pred="predicated", access="grid", items_per_thread=2, block=256, prefetch=1),
+               dict()):
+        assert_same(ctx.query(plan, pv.variant(**kw)), w, ctxmsg=str(kw))
+    plan = workloads.filter_project_plan()
+    w = _oracle(plan, t)
+    for kw in (dict(exec="single", pred="branch", access="grid", items_per_thread=4, block=256, prefetch=1),
+               dict(exec="multi", pred="predicated", access="grid", items_per_thread=4, block=256, prefetch=1),
+               dict(exec="multi", pred="branch", access="chunked", items_per_thread=2, block=512)):
+        assert_same(ctx.query(plan, pv.variant(**kw)), w, ordered=kw["exec"] == "multi", ctxmsg=str(kw))
+
+
+def test_lowcard_grouped_6m_rows(ctx):
+    li = {"li": datagen.table_lowcard_groups(6_000_000)}
+    _register_host(ctx, li)
+    plan = workloads.lowcard_plan()
+    w = _oracle(plan, li)
+    for kw in (dict(agg="local", ht="perfect", threads_per_table=1, pred="predicated", items_per_thread=1,
+                    block=256, prefetch=1),   # the benchmark's variant
+               dict(agg="local", ht="perfect", pred="branch", items_per_thread=1, block=512),
+               dict(agg="global", ht="linear", pred="predicated", items_per_thread=1),
+               dict(agg="local", ht="cuckoo", exec="multi", items_per_thread=1)):
+        assert_same(ctx.query(plan, pv.variant(**kw)), w, ctxmsg=str(kw))
+
+
+def _keyval_60m(ctx, g, dist):
+    import torch
+    n = 60_000_000
+    if dist == "uniform":
+        key = datagen.uniform_int_torch(datagen.DEFAULT_SEED, 301, n, 0, g, torch.int32, device="cuda")
+    else:
+        key = datagen.zipf_keys_torch(datagen.DEFAULT_SEED, 302, n, g, device="cuda")
+    val = datagen.uniform_int_torch(datagen.DEFAULT_SEED, 303, n, 0, 1_000_000, torch.int64, device="cuda")
+    ctx.register_table("kv", {"key": key, "val": val})
+    host = {"kv": {"key": key.cpu().numpy(), "val": val.cpu().numpy()}}
+    return host, (key, val)
+
+
+@pytest.mark.parametrize("g,dist,variants", [
+    (1000, "uniform", [dict(agg="local", ht="perfect", pred="branch", items_per_thread=1, block=256, prefetch=1),
+                       dict(agg="local", ht="linear", items_per_thread=1)]),
+    (1_000_000, "zipf", [dict(agg="global", ht="perfect", pred="branch", items_per_thread=1, block=256),
+                         dict(agg="global", ht="cuckoo", exec="multi", items_per_thread=1)]),
+])
+def test_keyval_60m_rows(ctx, g, dist, variants):
+    host, keep = _keyval_60m(ctx, g, dist)
+    plan = workloads.keyval_plan()
+    w = _oracle(plan, host)
+    assert len(w[0]) <= g and int(w[2].sum()) == 60_000_000
+    for kw in variants:
+        assert_same(ctx.query(plan, pv.variant(**kw)), w, ctxmsg=str(kw))
+
+
+def test_star_join_60m_rows(ctx):
+    import torch
+    n = 60_000_000
+    s = {name: datagen.star_dimension(name, rows, gg) for name, rows, gg in datagen.STAR_DIMS}
+    fact = {"fk_" + name[2:]: datagen.uniform_int_torch(datagen.DEFAULT_SEED, 501 + j, n, 0, rows, torch.int32,
+                                                         device="cuda")
+            for j, (name, rows, _) in enumerate(datagen.STAR_DIMS)}
+    fact["revenue"] = datagen.uniform_int_torch(datagen.DEFAULT_SEED, 509, n, 100, 10_000_000, torch.int64,
+                                                device="cuda")
+    ctx.register_table("fact", fact)
+    _register_host(ctx, s)
+    host = {"fact": {c: v.cpu().numpy() for c, v in fact.items()}, **s}
+    plan = workloads.star_plan()
+    w = _oracle(plan, host)
+    assert len(w[0]) > 100
+    for kind, kw in (("perfect", dict(agg="local", ht="perfect", pred="branch", items_per_thread=1, block=512)),
+                     ("linear", dict(agg="global", ht="linear", pred="predicated", items_per_thread=1, prefetch=1)),
+                     ("cuckoo", dict(agg="local", ht="perfect", pred="branch", items_per_thread=1, block=256))):
+        assert_same(ctx.query(plan, pv.variant(**kw), pv.ht_variant(kind)), w, ctxmsg=f"{kind} {kw}")
