@@ -220,7 +220,8 @@ def time_query(data: SuiteData, q: dict, reps: int = 3) -> dict:
     return out
 
 
-def algorithm1_config(train: list, timings: dict, grid: list, q_sweeps: int = 3) -> dict:
+def algorithm1_config(train: list, timings: dict, grid: list, q_sweeps: int = 3, counts: dict | None = None,
+                      name: str = "") -> dict:
     """Per-workload configuration (Section 8.3): Algorithm 1 over the grid's
     dimensions with the workload time = the sum of the training queries'
     times (looked up from the exhaustive timings; a variant missing from the
@@ -234,14 +235,18 @@ def algorithm1_config(train: list, timings: dict, grid: list, q_sweeps: int = 3)
                 vals.append(v[n])
         dims.append((n, vals))
     keys = {autotune.variant_key(v) for v in grid}
+    evaluated = set()
 
     def cost(v):
         k = autotune.variant_key(v)
+        evaluated.add(k)
         if k not in keys:
             return math.inf
         return sum(timings[q["id"]].get(k, math.inf) for q in train)
 
     v, c, n = autotune.feature_wise(cost, dims, q=q_sweeps)
+    if counts is not None:
+        counts[name] = sum(1 for k in evaluated if k in keys)
     return v
 
 
@@ -337,7 +342,9 @@ def judge(ctx: "pv.Context", ex: dict, n_train: int | None = None, candidates=CA
     X, y = _rows(train, stats, timings)
     model, hist = _fit(ctx, X, y, *chosen, seed)
     t_train = time.time() - t1
-    configs = {g: algorithm1_config([q for q in train if grid_key(q) == g], timings, GRIDS[g]) for g in GRIDS}
+    alg1_runs = {}
+    configs = {g: algorithm1_config([q for q in train if grid_key(q) == g], timings, GRIDS[g], counts=alg1_runs, name=g)
+               for g in GRIDS}
     per_query = _evaluate(model, test, stats, timings, configs, top_k)
     r_pick = np.array([p["pick_ms"] / p["best_ms"] for p in per_query])
     r_topk = np.array([p["topk_ms"] / p["best_ms"] for p in per_query])
@@ -354,7 +361,8 @@ def judge(ctx: "pv.Context", ex: dict, n_train: int | None = None, candidates=CA
         f"mlp_top{top_k}_within_10pct": float(np.mean(r_topk <= 1.10)),
         f"mlp_top{top_k}_geomean_slowdown": gm(r_topk),
         "alg1_within_10pct": float(np.mean(r_cfg <= 1.10)), "alg1_geomean_slowdown": gm(r_cfg),
-        "alg1_worst_slowdown": float(r_cfg.max()), "alg1_configs": configs, "per_query": per_query,
+        "alg1_worst_slowdown": float(r_cfg.max()), "alg1_configs": configs,
+        "alg1_variants_run": alg1_runs, "per_query": per_query,
     }
 
 
