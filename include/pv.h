@@ -193,6 +193,13 @@ pv_status pv_column_stats(pv_ctx* ctx, pv_col col, int64_t* min_out, int64_t* ma
 pv_status pv_build_hash_table(pv_ctx* ctx, const pv_build_spec* spec, const pv_ht_variant* var,
                               pv_ht* out);
 
+/* Enqueues the build pipeline of an existing table again into the same slots
+ * (clear, insert, duplicate check) after its input columns changed in place.
+ * Allocates nothing and does not synchronise, so it may be recorded by
+ * pv_graph_capture_begin/end together with the pipelines that probe the table;
+ * the payload statistics of the first build (perfect-array domains) are kept. */
+pv_status pv_rebuild_hash_table(pv_ctx* ctx, pv_ht ht);
+
 /* ---- probe / scan pipelines --------------------------------------------- */
 
 /* Enqueues the pipeline program under the variant and returns a ctx-owned
@@ -226,7 +233,7 @@ pv_status pv_free(pv_ctx* ctx, int32_t handle);
 
 /* ---- CUDA graphs -------------------------------------------------------- */
 
-/* Records every pv_rerun (and pv_l2_flush) enqueued between begin and end
+/* Records every pv_rerun, pv_rebuild_hash_table (and pv_l2_flush) enqueued between begin and end
  * into one CUDA graph, replayed by pv_graph_launch on the ctx stream (many
  * small pipelines without per-launch overhead).  No other pv call may run
  * in between. */

@@ -9,14 +9,6 @@
 
 namespace pv {
 
-struct BuildParams {
-  BuildInput in;
-  DevHT ht;
-  int max_evictions;
-  int32_t* err;
-  unsigned long long* pay_stats;  // [2]: max code, min code of the payload
-};
-
 __device__ __forceinline__ int64_t load_any(const void* p, int type, int64_t r) {
   if (type == PV_I32) return static_cast<const int32_t*>(p)[r];
   if (type == PV_I64) return static_cast<const int64_t*>(p)[r];
@@ -197,31 +189,22 @@ pv_status build_table(const BuildEnv& env, const BuildInput& in, const pv_ht_var
   }
   h.slots = static_cast<uint64_t*>(out.mem);
   unsigned long long* stats = reinterpret_cast<unsigned long long*>(static_cast<char*>(out.mem) + ((bytes + 15) & ~size_t(15)));
-  cudaError_t e = cudaMemsetAsync(h.slots, var.kind == PV_HT_PERFECT ? 0 : 0xFF, bytes, env.stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(stats, 0, 16, env.stream);
-  if (e != cudaSuccess) {
-    msg = cudaGetErrorString(e);
-    return PV_ERR_CUDA;
-  }
-  BuildParams bp{};
+  out.slot_bytes = bytes;
+  BuildParams& bp = out.bp;
+  bp = BuildParams{};
   bp.in = in;
   bp.ht = h;
   bp.max_evictions = max_ev;
   bp.err = env.err;
   bp.pay_stats = stats;
-  if (in.n_rows > 0) {
-    const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(env.sm_count * 8, (in.n_rows + 255) / 256)));
-    k_build<<<grid, 256, 0, env.stream>>>(bp);
-    ++*env.launches;
-    if (var.kind == PV_HT_CUCKOO) {
-      const int g2 = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(env.sm_count * 8, (h.cap + 255) / 256)));
-      k_cuckoo_dupcheck<<<g2, 256, 0, env.stream>>>(h, env.err);
-      ++*env.launches;
-    }
+  pv_status st = rebuild_table(env, out);
+  if (st != PV_OK) {
+    msg = "build launch failed";
+    return st;
   }
+  cudaError_t e = cudaSuccess;
   unsigned long long hs[2] = {0, 0};
-  e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaMemcpyAsync(hs, stats, 16, cudaMemcpyDeviceToHost, env.stream);
+  e = cudaMemcpyAsync(hs, stats, 16, cudaMemcpyDeviceToHost, env.stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(env.stream);
   if (e != cudaSuccess) {
     msg = cudaGetErrorString(e);
@@ -237,6 +220,25 @@ pv_status build_table(const BuildEnv& env, const BuildInput& in, const pv_ht_var
     }
   }
   return PV_OK;
+}
+
+pv_status rebuild_table(const BuildEnv& env, const BuildTable& t) {
+  const BuildParams& bp = t.bp;
+  const DevHT& h = bp.ht;
+  cudaError_t e = cudaMemsetAsync(h.slots, h.kind == PV_HT_PERFECT ? 0 : 0xFF, t.slot_bytes, env.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bp.pay_stats, 0, 16, env.stream);
+  if (e != cudaSuccess) return PV_ERR_CUDA;
+  if (bp.in.n_rows > 0) {
+    const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(env.sm_count * 8, (bp.in.n_rows + 255) / 256)));
+    k_build<<<grid, 256, 0, env.stream>>>(bp);
+    ++*env.launches;
+    if (h.kind == PV_HT_CUCKOO) {
+      const int g2 = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(env.sm_count * 8, (h.cap + 255) / 256)));
+      k_cuckoo_dupcheck<<<g2, 256, 0, env.stream>>>(h, env.err);
+      ++*env.launches;
+    }
+  }
+  return cudaGetLastError() == cudaSuccess ? PV_OK : PV_ERR_CUDA;
 }
 
 }  // namespace pv

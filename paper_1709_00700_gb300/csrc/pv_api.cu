@@ -795,6 +795,17 @@ pv_status pv_build_hash_table(pv_ctx* c, const pv_build_spec* spec, const pv_ht_
   return PV_OK;
 }
 
+pv_status pv_rebuild_hash_table(pv_ctx* c, pv_ht h) {
+  if (!c) return PV_ERR_INVALID_ARG;
+  auto it = c->tables.find(h);
+  if (it == c->tables.end()) return fail(c, PV_ERR_INVALID_ARG, "unknown hash table handle");
+  BuildEnv env{c->stream, c->sm_count, c->d_err, &c->launches,
+               [](size_t b, void* u) { return dalloc(static_cast<pv_ctx*>(u), b); }, c};
+  c->launches = 0;
+  pv_status s = rebuild_table(env, *it->second);
+  return s == PV_OK ? s : fail(c, s, "rebuild launch failed");
+}
+
 pv_status pv_run_pipeline(pv_ctx* c, const pv_pipeline_spec* spec, const pv_variant* var, pv_res* out) {
   if (!c || !spec || !var || !out) return PV_ERR_INVALID_ARG;
   if (c->capturing) return fail(c, PV_ERR_INVALID_ARG, "pv_run_pipeline allocates; capture pv_rerun instead");

@@ -10,14 +10,6 @@
 
 namespace pv {
 
-struct BuildTable {
-  DevHT ht{};
-  int n_payload = 0;
-  int64_t pay_min[PV_MAX_PAYLOAD]{};  // over the surviving rows (empty: min > max)
-  int64_t pay_max[PV_MAX_PAYLOAD]{};
-  void* mem = nullptr;
-};
-
 struct BuildInput {
   int64_t n_rows;
   const void* key;
@@ -29,6 +21,24 @@ struct BuildInput {
   int n_payload;
   const void* pay_col[PV_MAX_PAYLOAD];
   int pay_type[PV_MAX_PAYLOAD];
+};
+
+struct BuildParams {
+  BuildInput in;
+  DevHT ht;
+  int max_evictions;
+  int32_t* err;
+  unsigned long long* pay_stats;  // [2]: max code, min code of the payload
+};
+
+struct BuildTable {
+  DevHT ht{};
+  int n_payload = 0;
+  int64_t pay_min[PV_MAX_PAYLOAD]{};  // over the surviving rows (empty: min > max)
+  int64_t pay_max[PV_MAX_PAYLOAD]{};
+  void* mem = nullptr;
+  size_t slot_bytes = 0;  // bytes of the slot array (rebuilds clear them)
+  BuildParams bp{};       // the build pipeline, kept for rebuilds
 };
 
 struct BuildEnv {
@@ -45,5 +55,10 @@ struct BuildEnv {
 // (duplicate key, full table, cuckoo cycle) land in env.err.
 pv_status build_table(const BuildEnv& env, const BuildInput& in, const pv_ht_variant& var, int64_t kmin,
                       int64_t kmax, BuildTable& out, std::string& msg);
+
+// Enqueues the build pipeline of an existing table again (clear, insert,
+// duplicate check): no allocation, no synchronisation; the payload
+// statistics of the first build are kept.
+pv_status rebuild_table(const BuildEnv& env, const BuildTable& t);
 
 }  // namespace pv

@@ -97,6 +97,7 @@ _SIGS = {
                                             ctypes.c_void_p, ctypes.c_int64, _P(ctypes.c_int32)]),
     "pv_column_stats": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, _P(ctypes.c_int64), _P(ctypes.c_int64)]),
     "pv_build_hash_table": (ctypes.c_int32, [ctypes.c_void_p, _P(pv_build_spec), _P(pv_ht_variant), _P(ctypes.c_int32)]),
+    "pv_rebuild_hash_table": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
     "pv_run_pipeline": (ctypes.c_int32, [ctypes.c_void_p, _P(pv_pipeline_spec), _P(pv_variant), _P(ctypes.c_int32)]),
     "pv_rerun": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
     "pv_sync": (ctypes.c_int32, [ctypes.c_void_p]),
@@ -331,6 +332,9 @@ class Context:
             s.proj[i] = ref(r)
         s.capacity_hint = int(plan.get("capacity_hint", 0))
         return s
+
+    def rebuild(self, ht: int):
+        self._check(self.lib.pv_rebuild_hash_table(self.h, ht))
 
     def build_all(self, plan: dict, htv: pv_ht_variant) -> list:
         return [self.build(b, htv) for b in plan.get("builds", [])]

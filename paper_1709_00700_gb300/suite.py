@@ -385,8 +385,13 @@ def main(argv=None):
     ap.add_argument("--timings-in", default="", help="judge saved exploration results instead of timing again")
     ap.add_argument("--timings-out", default="")
     ap.add_argument("--out", default="")
+    ap.add_argument("--graphs", action="store_true", help="run the CUDA-graph batch experiment only")
     a = ap.parse_args(argv)
     ctx = pv.Context(0)
+    if a.graphs:
+        print(json.dumps(graph_experiment(ctx)))
+        ctx.close()
+        return
     if a.timings_in:
         with open(a.timings_in) as f:
             ex = json.load(f)
@@ -404,6 +409,87 @@ def main(argv=None):
         with open(a.out, "w") as f:
             json.dump(summary, f)
     ctx.close()
+
+
+
+def graph_experiment(ctx: "pv.Context", n_queries: int = 64, rows: int = 1_000_000, reps: int = 20) -> dict:
+    """CUDA graphs for many small pipelines: n_queries filter/aggregate queries
+    (different constants, one shape) on a rows-row table replayed eagerly
+    (one pv_rerun each) and as one captured graph; and a star join's four
+    build pipelines plus its probe pipeline, eager and as one graph."""
+    import torch
+    dev = f"cuda:{ctx.device}"
+    u = datagen.uniform_int_torch
+    seed = datagen.DEFAULT_SEED
+    ctx.register_table("g", {"a": u(seed, 101, rows, 0, 100, torch.int32, device=dev),
+                             "b": u(seed, 102, rows, 0, 100, torch.int32, device=dev),
+                             "price": u(seed, 103, rows, 100, 10_000_000, torch.int64, device=dev)})
+    rng = np.random.default_rng(7)
+    var = pv.variant(pred="branch", access="grid", items_per_thread=4, block=512, grid_mult=2)
+    results = []
+    for _ in range(n_queries):
+        lo = int(rng.integers(0, 60))
+        plan = {"fact": "g", "filters": [["a", "lt", int(rng.integers(1, 100))], ["b", "between", lo, lo + 30]],
+                "aggs": [["sum", [["x", "price"]]], ["count"]]}
+        results.append(ctx.run(plan, var))
+    ctx.sync()
+    st = ctx.stream
+
+    def timed(fn):
+        ms = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            fn()
+            b.record(st)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return float(np.median(ms))
+
+    eager = timed(lambda: [ctx.rerun(r) for r in results])
+    want = [[int(c[0]) for c in ctx.fetch(r)] for r in results]
+    gb = autotune.GraphBatch(ctx, results)
+    graph = timed(gb.launch)
+    got = [[int(c[0]) for c in ctx.fetch(r)] for r in results]
+    assert got == want, "graph replay changed a result"
+    gb.free()
+    for r in results:
+        ctx.free(r)
+    # star join: builds + probe as one graph
+    s = datagen.star_schema(rows)
+    for t, cols in s.items():
+        ctx.register_table(t, {c: torch.from_numpy(v).to(dev) for c, v in cols.items()})
+    plan = workloads.star_plan()
+    hts = ctx.build_all(plan, pv.ht_variant("perfect"))
+    res = ctx.run(plan, pv.variant(agg="local", ht="perfect", items_per_thread=1, block=512), hts)
+    ctx.sync()
+
+    def star_eager():
+        for h in hts:
+            ctx.rebuild(h)
+        ctx.rerun(res)
+
+    star_e = timed(star_eager)
+    ctx.sync()
+    ctx._check(ctx.lib.pv_graph_capture_begin(ctx.h))
+    star_eager()
+    g = ctypes_graph_end(ctx)
+    star_g = timed(lambda: ctx._check(ctx.lib.pv_graph_launch(ctx.h, g)))
+    ctx.sync()
+    ctx.free(g)
+    ctx.free(res)
+    for h in hts:
+        ctx.free(h)
+    return {"queries": n_queries, "rows": rows, "eager_ms": eager, "graph_ms": graph,
+            "eager_us_per_query": 1000 * eager / n_queries, "graph_us_per_query": 1000 * graph / n_queries,
+            "star_build_probe_rows": rows, "star_eager_ms": star_e, "star_graph_ms": star_g}
+
+
+def ctypes_graph_end(ctx) -> int:
+    import ctypes
+    g = ctypes.c_int32()
+    ctx._check(ctx.lib.pv_graph_capture_end(ctx.h, ctypes.byref(g)))
+    return g.value
 
 
 if __name__ == "__main__":

@@ -361,3 +361,43 @@ def test_cuda_malloc_async_allocator():
     register(c, t)
     assert_same(c.query(workloads.filter_agg_plan(), pv.variant()), want(workloads.filter_agg_plan(), t))
     c.close()
+
+
+def test_rebuild_after_in_place_change_and_in_a_graph(ctx):
+    import ctypes
+    import torch
+    D, r = 1000, 4
+    dim = {"key": torch.arange(D, dtype=torch.int32, device="cuda"),
+           "f": (torch.arange(D, device="cuda") % 100).to(torch.int32),
+           "g": (torch.arange(D, device="cuda") % 7).to(torch.int32)}
+    fact = {"fk": (torch.arange(D * r, device="cuda") % D).to(torch.int32),
+            "v": torch.ones(D * r, dtype=torch.int64, device="cuda")}
+    ctx.register_table("rdim", dim)
+    ctx.register_table("rfact", fact)
+    plan = {"fact": "rfact", "builds": [{"table": "rdim", "key": "key", "filters": [["f", "lt", 30]], "payload": []}],
+            "probes": [{"build": 0, "fk": "fk"}], "aggs": [["count"]]}
+    for kind in ("linear", "cuckoo", "perfect"):
+        hts = ctx.build_all(plan, pv.ht_variant(kind))
+        res = ctx.run(plan, pv.variant(), hts)
+        assert int(ctx.fetch(res)[0][0]) == r * 300
+        dim["f"].copy_((torch.arange(D, device="cuda") * 7 % 100).to(torch.int32))  # in place
+        host = {"rdim": {k: v.cpu().numpy() for k, v in dim.items()},
+                "rfact": {k: v.cpu().numpy() for k, v in fact.items()}}
+        expect = int(want(plan, host)[0][0])
+        ctx.rebuild(hts[0])
+        ctx.rerun(res)
+        assert int(ctx.fetch(res)[0][0]) == expect
+        # the same rebuild + probe recorded as one graph
+        dim["f"].copy_((torch.arange(D, device="cuda") % 100).to(torch.int32))
+        ctx.sync()
+        assert ctx.lib.pv_graph_capture_begin(ctx.h) == 0
+        ctx.rebuild(hts[0])
+        ctx.rerun(res)
+        g = ctypes.c_int32()
+        assert ctx.lib.pv_graph_capture_end(ctx.h, ctypes.byref(g)) == 0
+        assert ctx.lib.pv_graph_launch(ctx.h, g.value) == 0
+        assert int(ctx.fetch(res)[0][0]) == r * 300
+        ctx.free(g.value)
+        ctx.free(res)
+        for h in hts:
+            ctx.free(h)
