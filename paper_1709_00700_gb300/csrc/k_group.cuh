@@ -283,29 +283,40 @@ struct SinkLocalPerfect {
 // instead of masking every value.
 template <class SH>
 struct SinkThreadPerfect {
+  // Tables of 256 threads x (cap x 16 B units) let three CTAs share an SM;
+  // the predicated loop then runs without register double buffering.
+  static constexpr int kRegs = 80;
+  static constexpr bool kPipelined = false;
   using A = typename SH::Aggs;
   static constexpr int NA = A::N;
   static constexpr int CA = count_index<A>();
   static constexpr int SW = ((CA >= 0 ? NA : NA + 1) + 1) & ~1;
   static constexpr int SP = SW / 2;
-  static __host__ __device__ int64_t units_per_thread(int64_t cap) { return (cap + 1) * SP; }
+  static __host__ __device__ int64_t units_per_thread(int64_t cap) { return cap * SP; }
+  static __host__ __device__ size_t smem_bytes(int64_t cap, int block) {
+    return static_cast<size_t>(units_per_thread(cap)) * 16 * block;
+  }
   template <int W>
   static __device__ __forceinline__ constexpr int word_func() {
     if constexpr (W < NA) return A::func_of[W];
     else return PV_SUM;
   }
   const GroupDesc& gd; const GroupOut& g; int32_t* err; ulonglong2* sm;
+  uint32_t sbase;        // shared address of this thread's unit 0 of slot 0
+  uint32_t ustride;      // bytes between a thread's consecutive units
+  bool bad = false;      // a live row's key fell outside the domain
   __device__ SinkThreadPerfect(const GroupDesc& d, const GroupOut& o, int32_t* e, unsigned long long* s)
-      : gd(d), g(o), err(e), sm(reinterpret_cast<ulonglong2*>(s)) {}
+      : gd(d), g(o), err(e), sm(reinterpret_cast<ulonglong2*>(s)),
+        sbase(static_cast<uint32_t>(__cvta_generic_to_shared(s)) + threadIdx.x * 16u), ustride(blockDim.x * 16u) {}
   __device__ void init() {
     const int64_t n = units_per_thread(g.cap);
     for (int64_t u = 0; u < n; ++u) sm[u * blockDim.x + threadIdx.x] = make_ulonglong2(0, 0);
   }
   __device__ __forceinline__ void add(Item<SH>& it, const KParams& kp, int r, bool live) {
     bool ok;
-    uint64_t s = row_perfect_index<SH>(gd, it, kp, r, ok);
-    if (!ok && live) set_error(err, PV_ERR_KEY_OUT_OF_RANGE);
-    s = (ok && live) ? s : static_cast<uint64_t>(g.cap);
+    const uint64_t s = row_perfect_index<SH>(gd, it, kp, r, ok);
+    bad |= !ok && live;
+    if (!(ok && live)) return;
     uint64_t v[SW];
     static_for<SW>([&](auto w) {
       constexpr int I = decltype(w)::value;
@@ -316,16 +327,25 @@ struct SinkThreadPerfect {
         v[I] = (CA < 0 && I == NA) ? 1ull : 0ull;
       }
     });
-    ulonglong2* p = sm + static_cast<uint32_t>(s) * SP * blockDim.x + threadIdx.x;
+    // unit J of slot s: sbase + (s * SP + J) * ustride; volatile asm keeps
+    // each read-modify-write in program order (rows may share a slot)
+    const uint32_t a = sbase + static_cast<uint32_t>(s) * (SP * ustride);
+    const uint32_t us = ustride;
+    unsigned long long w[SW];
     static_for<SP>([&](auto j) {
       constexpr int J = decltype(j)::value;
-      ulonglong2 c = p[J * blockDim.x];
-      c.x = acc_combine<word_func<2 * J>()>(c.x, v[2 * J]);
-      c.y = acc_combine<word_func<2 * J + 1>()>(c.y, v[2 * J + 1]);
-      p[J * blockDim.x] = c;
+      asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(w[2 * J]), "=l"(w[2 * J + 1]) : "r"(a + J * us)
+                   : "memory");
+    });
+    static_for<SP>([&](auto j) {
+      constexpr int J = decltype(j)::value;
+      const unsigned long long x = acc_combine<word_func<2 * J>()>(w[2 * J], v[2 * J]);
+      const unsigned long long y = acc_combine<word_func<2 * J + 1>()>(w[2 * J + 1], v[2 * J + 1]);
+      asm volatile("st.shared.v2.u64 [%0], {%1, %2};" ::"r"(a + J * us), "l"(x), "l"(y) : "memory");
     });
   }
   __device__ void finish() {
+    if (bad) set_error(err, PV_ERR_KEY_OUT_OF_RANGE);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const unsigned long long* w64 = reinterpret_cast<const unsigned long long*>(sm);
@@ -469,8 +489,17 @@ __device__ __forceinline__ void extract_slots(const GroupDesc& gd, const GroupOu
 // ---------------------------------------------------------------------------
 // Kernels
 // ---------------------------------------------------------------------------
+// Register cap and loop form of a sink: 128 registers and the software-
+// pipelined predicated loop unless the sink states otherwise.
+template <class S, class = void> struct SinkRegs { static constexpr int value = 128; };
+template <class S> struct SinkRegs<S, std::void_t<decltype(S::kRegs)>> { static constexpr int value = S::kRegs; };
+template <class S, class = void> struct SinkPipelined { static constexpr bool value = true; };
+template <class S> struct SinkPipelined<S, std::void_t<decltype(S::kPipelined)>> {
+  static constexpr bool value = S::kPipelined;
+};
+
 template <class SH, bool PRED, bool CHUNK, int U, class Sink>
-__global__ void __maxnreg__(128) k_group(const __grid_constant__ KParams kp, const __grid_constant__ GroupDesc gd, const __grid_constant__ GroupOut g) {
+__global__ void __maxnreg__(SinkRegs<Sink>::value) k_group(const __grid_constant__ KParams kp, const __grid_constant__ GroupDesc gd, const __grid_constant__ GroupOut g) {
   extern __shared__ unsigned long long smem[];
   if (blockIdx.x == 0 && threadIdx.x == 0) *g.out_count = 0;  // extraction runs after this kernel
   Sink sink(gd, g, kp.err, smem);
@@ -486,8 +515,23 @@ __global__ void __maxnreg__(128) k_group(const __grid_constant__ KParams kp, con
       }
     }
   };
-  if constexpr (PRED) {
+  if constexpr (PRED && SinkPipelined<Sink>::value) {
     for_items_pipelined<SH, CHUNK, U>(kp, consume);
+  } else if constexpr (PRED && !CHUNK) {
+    for_items_pred<SH, U>(kp, [&](Item<SH>& it, auto full) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const bool live = (it.mask >> r) & 1u;
+        if constexpr (decltype(full)::value) sink.add(it, kp, r, live);
+        else if (r < it.nvalid) sink.add(it, kp, r, live);
+      }
+    });
+  } else if constexpr (PRED) {
+    for_items<CHUNK, U>(kp.n_items, [&](const int64_t (&idx)[U]) {
+      Item<SH> it[U];
+      eval_items<SH, PRED, U>(it, kp, idx);
+      consume(it);
+    });
   } else {
     for_items<CHUNK, U>(kp.n_items, [&](const int64_t (&idx)[U]) {
       Item<SH> it[U];
@@ -604,7 +648,7 @@ static pv_status launch_group(const LaunchCfg& c, const KParams& kp, const Group
     if (!local) {
       s = run_group<SH, UMASK, SinkGlobalPerfect>(c, kp, gd, g, 0);
     } else if (v.threads_per_table == 1) {
-      const size_t smem = static_cast<size_t>(SinkThreadPerfect<SH>::units_per_thread(g.cap)) * 16 * c.block;
+      const size_t smem = SinkThreadPerfect<SH>::smem_bytes(g.cap, c.block);
       if (smem > 200 * 1024) return PV_ERR_UNSUPPORTED;
       s = run_group<SH, UMASK, SinkThreadPerfect>(c, kp, gd, g, smem);
     } else {

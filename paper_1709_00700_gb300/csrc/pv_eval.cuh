@@ -2,6 +2,8 @@
 // warp-uniform item loop, shared by the scan and the grouped kernels.
 #pragma once
 
+#include <type_traits>
+
 #include "pv_internal.h"
 
 namespace pv {
@@ -135,26 +137,47 @@ __device__ __forceinline__ void filter_probe_items(Item<SH> (&it)[U], const KPar
   });
 }
 
+// log2 of the bytes one item (4 rows) of each column occupies, 4 bits per
+// column.
+template <class L> struct ItemShifts;
+template <class... Ts> struct ItemShifts<TList<Ts...>> {
+  static constexpr uint32_t log2c(uint32_t x) { return x <= 1 ? 0 : 1 + log2c(x >> 1); }
+  static constexpr uint64_t value = [] {
+    uint64_t p = 0;
+    int i = 0;
+    ((p |= static_cast<uint64_t>(log2c(4 * sizeof(typename Ts::T))) << (4 * i++)), ...);
+    return p;
+  }();
+};
+
 // Bulk prefetch into L2 (TMA engine, no registers or shared memory used) of
-// the 128 rows a warp consumes at one trip, for every column the pipeline
-// loads.  Called by one lane; only whole in-bounds chunks are prefetched
-// (16-byte aligned: column bases are 16-byte aligned and 128 rows of any
-// column type are a multiple of 16 bytes).
+// the 32 items (128 rows) a warp consumes at one trip, spread over the
+// lanes: lane c prefetches column c.  Only whole in-range chunks are
+// prefetched (16-byte aligned: column bases are 16-byte aligned and 128 rows
+// of any column type are a multiple of 16 bytes).
 template <class SH>
-__device__ __forceinline__ void prefetch_warp_chunk(const KParams& kp, int64_t first_item) {
-  if (first_item < 0 || (first_item + 32) * 4 > kp.n_rows) return;
-  static_for<SH::Cols::N>([&](auto s) {
-    constexpr int S = decltype(s)::value;
-    using T = typename At<S, typename SH::Cols::L>::type::T;
-    const char* p = static_cast<const char*>(kp.col[S]) + first_item * 4 * static_cast<int64_t>(sizeof(T));
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(static_cast<uint32_t>(128 * sizeof(T)))
-                 : "memory");
-  });
-}
+struct LanePrefetch {
+  static_assert(SH::Cols::N <= 16, "one lane per column, 4-bit shifts");
+  const char* base = nullptr;
+  uint32_t shift = 0;
+  __device__ __forceinline__ LanePrefetch(const KParams& kp, int lane) {
+    if (lane < SH::Cols::N) {
+      base = static_cast<const char*>(kp.col[lane]);
+      shift = static_cast<uint32_t>(ItemShifts<typename SH::Cols::L>::value >> (4 * lane)) & 15u;
+    }
+  }
+  // first_item: the warp's first item of the chunk; n_full: items with 4 rows.
+  __device__ __forceinline__ void issue(int64_t first_item, int64_t n_full) const {
+    if (base != nullptr && first_item >= 0 && first_item + 32 <= n_full) {
+      const char* p = base + (first_item << shift);
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(32u << shift) : "memory");
+    }
+  }
+};
 
 // Grid-stride item loop (as for_items) that also bulk-prefetches into L2
-// the chunk its warp will read kp.prefetch trips later (lane 0 of a warp runs
-// every trip any lane of the warp runs).  Chunked access: no prefetch.
+// the chunk its warp will read kp.prefetch trips later.  Chunked access: no
+// prefetch.
 template <class SH, bool CHUNK, int U, class F>
 __device__ __forceinline__ void for_items_pf(const KParams& kp, F&& f) {
   const int pf = CHUNK ? 0 : kp.prefetch;
@@ -165,13 +188,13 @@ __device__ __forceinline__ void for_items_pf(const KParams& kp, F&& f) {
   const int64_t T = static_cast<int64_t>(gridDim.x) * blockDim.x;
   const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
+  const int64_t n_full = kp.n_rows >> 2;
+  const LanePrefetch<SH> lp(kp, lane);
   auto prefetch = [&](int64_t k) {
-    if (lane == 0) {
 #pragma unroll
-      for (int u = 0; u < U; ++u) prefetch_warp_chunk<SH>(kp, (t - lane) + (k * U + u) * T);
-    }
+    for (int u = 0; u < U; ++u) lp.issue((t - lane) + (k * U + u) * T, n_full);
   };
-  for (int d = 1; d <= pf; ++d) prefetch(d);
+  for (int d = 1; d < pf; ++d) prefetch(d);
   int64_t k = 0;
   for (int64_t base = t; base < kp.n_items; base += U * T, ++k) {
     prefetch(k + pf);
@@ -179,6 +202,53 @@ __device__ __forceinline__ void for_items_pf(const KParams& kp, F&& f) {
 #pragma unroll
     for (int u = 0; u < U; ++u) idx[u] = base + u * T;
     f(idx);
+  }
+}
+
+// Predicated grid-stride item loop without register double buffering.
+// Trips whose U items all hold 4 rows load every column with no bounds
+// checks and call consume(item, std::true_type); the thread's remaining
+// items (at most the one partial item of the table and items past the
+// full ones) follow with consume(item, std::false_type).  Prefetch as in
+// for_items_pf.
+template <class SH, int U, class F>
+__device__ __forceinline__ void for_items_pred(const KParams& kp, F&& consume) {
+  const int64_t T = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int64_t n_full = kp.n_rows >> 2;
+  const int pf = kp.prefetch;
+  const LanePrefetch<SH> lp(kp, lane);
+  constexpr uint32_t all = SH::Where::slots | SH::Probes::slots | SH::rest_slots;
+  if (pf > 0) {
+    for (int d = 1; d < pf; ++d)
+#pragma unroll
+      for (int u = 0; u < U; ++u) lp.issue((t - lane) + static_cast<int64_t>(d * U + u) * T, n_full);
+  }
+  int64_t base = t;
+  int64_t pfb = (t - lane) + static_cast<int64_t>(pf) * U * T;  // warp chunk prefetched at this trip
+  for (; base + (U - 1) * T < n_full; base += U * T, pfb += U * T) {
+    if (pf > 0) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) lp.issue(pfb + u * T, n_full);
+    }
+    Item<SH> it[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      it[u].nvalid = 4;
+      it[u].mask = 0xFu;
+      load_slots<SH, all>(it[u], kp, base + u * T);
+    }
+    filter_probe_items<SH, U>(it, kp);
+#pragma unroll
+    for (int u = 0; u < U; ++u) consume(it[u], std::true_type{});
+  }
+  for (; base < kp.n_items; base += T) {
+    Item<SH> one[1];
+    const int64_t idx[1] = {base};
+    load_items_all<SH, 1>(one, kp, idx);
+    filter_probe_items<SH, 1>(one, kp);
+    consume(one[0], std::false_type{});
   }
 }
 
@@ -212,12 +282,12 @@ __device__ __forceinline__ void for_items_pipelined(const KParams& kp, F&& consu
   if (!valid(0)) return;
   const int lane = threadIdx.x & 31;
   const int pf = CHUNK ? 0 : kp.prefetch;
+  const int64_t n_full = kp.n_rows >> 2;
+  const LanePrefetch<SH> lp(kp, lane);
   // trip k of this warp covers items (t - lane) + (k * U + u) * T, 32 per u
   auto prefetch = [&](int64_t k) {
-    if (lane == 0) {
 #pragma unroll
-      for (int u = 0; u < U; ++u) prefetch_warp_chunk<SH>(kp, (t - lane) + (k * U + u) * T);
-    }
+    for (int u = 0; u < U; ++u) lp.issue((t - lane) + (k * U + u) * T, n_full);
   };
   if (pf > 0) {
     for (int d = 1; d <= pf; ++d) prefetch(d);
