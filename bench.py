@@ -291,10 +291,52 @@ def barrier(dist):
         dist.barrier()
 
 
-def cpu_oracle_rate(plan, tables, budget_s: float, rows: int):
-    """The oracle as it stands, on all host cores, repeated for ~budget_s."""
+_OPS = {"lt": lambda v, c: v < c[0], "le": lambda v, c: v <= c[0], "gt": lambda v, c: v > c[0],
+        "ge": lambda v, c: v >= c[0], "eq": lambda v, c: v == c[0],
+        "between": lambda v, c: (v >= c[0]) & (v <= c[1])}
+
+
+def star_sector_bytes(tables, plan) -> int:
+    """Bytes the star join must read with lazy column loads: the first probe's
+    key column in full; every later key column and the aggregated column only
+    in the 32-byte sectors that hold at least one row still alive when it is
+    read (probes in plan order)."""
+    fact = tables[plan["fact"]]
+    n = len(next(iter(fact.values())))
+
+    def sectors(mask, elem):
+        per = 32 // elem
+        full = (n // per) * per
+        k = int(mask[:full].reshape(-1, per).any(axis=1).sum())
+        return 32 * (k + int(mask[full:].any()))
+
+    alive = np.ones(n, dtype=bool)
+    total = 0
+    for i, p in enumerate(plan["probes"]):
+        b = plan["builds"][p["build"]]
+        dim = tables[b["table"]]
+        keys = np.asarray(dim[b["key"]], dtype=np.int64)
+        ok = np.ones(len(keys), dtype=bool)
+        for col, op, *c in b.get("filters", []):
+            ok &= _OPS[op](np.asarray(dim[col], dtype=np.int64), c)
+        hit = np.zeros(int(keys.max()) + 1, dtype=bool)
+        hit[keys] = ok
+        size = np.asarray(fact[p["fk"]]).itemsize
+        fk = np.asarray(fact[p["fk"]], dtype=np.int64)
+        total += size * n if i == 0 else sectors(alive, size)
+        inside = (fk >= 0) & (fk < len(hit))
+        alive &= inside & hit[np.where(inside, fk, 0)]
+    for a in plan.get("aggs", []):
+        for term in (a[1] if len(a) > 1 else []):
+            total += sectors(alive, np.asarray(fact[term[1]]).itemsize)
+    return total
+
+
+def cpu_oracle_rate(plan, tables, budget_s: float, rows: int, threads: int = 0):
+    """The oracle as it stands, on all host cores (or `threads`), repeated for
+    ~budget_s."""
     from oracle import oracle
-    cores = oracle.hardware_threads()
+    cores = threads or oracle.hardware_threads()
     oracle.run(plan, tables, nthreads=cores)  # build + warm
     t0 = time.perf_counter()
     n = 0
@@ -315,7 +357,7 @@ def run_reference(args):
     rows = args.rows or w["rows"]
     tables, plan = make_tables(args.workload, rows, args.groups)
     from oracle import oracle
-    cores = oracle.hardware_threads()
+    cores = args.cpu_threads or oracle.hardware_threads()
     for _ in range(args.warmup):
         oracle.run(plan, tables, nthreads=cores)
     times = []
@@ -375,8 +417,9 @@ def run_pv(args):
     stream = ctx.stream
     clk = ClockSampler(local).start()
     clk.t_load = time.time()
+    flush = (lambda: None) if args.hot_l2 else (lambda: ctx.lib.pv_l2_flush(ctx.h))
     for _ in range(max(args.warmup, 1)):
-        ctx.lib.pv_l2_flush(ctx.h)
+        flush()
         ctx.rerun(res)
     ctx.sync()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -392,7 +435,7 @@ def run_pv(args):
         nv.__enter__()
     clk.t0 = time.time()
     for i in range(args.steps):
-        ctx.lib.pv_l2_flush(ctx.h)  # cold L2 before every step (outside the timed events)
+        flush()  # cold L2 before every step (outside the timed events), unless --hot-l2
         starts[i].record(stream)
         ctx.rerun(res)
         ends[i].record(stream)
@@ -408,7 +451,7 @@ def run_pv(args):
     ctx.set_kernel_timing(True)
     kernel_ms = []
     for i in range(max(3, min(args.steps, 20))):
-        ctx.lib.pv_l2_flush(ctx.h)
+        flush()
         ctx.rerun(res)
         kernel_ms.append(ctx.kernel_times())
     ctx.set_kernel_timing(False)
@@ -421,6 +464,9 @@ def run_pv(args):
     dom_ms = float(per_kernel[:, dom].mean())
     peak, peak_kind = measured_peaks()
     alg_bytes = w["bytes_per_row"] * rows
+    upper_bytes = None
+    if args.workload == "star":
+        upper_bytes, alg_bytes = alg_bytes, star_sector_bytes(tables, plan)
     achieved = alg_bytes / (dom_ms / 1000.0) / 1e9
     # end to end through the C ABI with host buffers: H2D of the step's input
     # columns from pinned memory, the pipeline, D2H of the result
@@ -447,7 +493,8 @@ def run_pv(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic (seeded counter-based generator)",
         "config": {"workload": w["desc"], "rows": rows, "variant": dict(var_kw, build=build_ht),
                    "tuning": tuning,
-                   "l2": "flushed (2x L2 write) before every step, outside the timed events",
+                   "l2": ("hot: no flush between steps, the inputs stay in L2 (hot-L2 numbers)" if args.hot_l2 else
+                          "flushed (2x L2 write, then discard) before every step, outside the timed events"),
                    "seed": datagen.DEFAULT_SEED, "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": ncu_traffic(args.workload),
@@ -458,8 +505,21 @@ def run_pv(args):
         "gpu_launches": (launches_per_step + 1) * args.steps,
         "clocks": nv.summary() if nv and nv.samples else clk.summary(),
     }
+    if upper_bytes is not None:
+        line["roofline"]["algorithmic_bytes_note"] = (
+            f"sector-exact: 32 B sectors of each column holding a row still alive when the column is read; "
+            f"every column in full would be {upper_bytes} B")
+    if args.workload == "keyval" and args.groups >= 1_000_000:
+        # global tables of 1e6+ groups are bound by random atomics: the same updates
+        # (one slot of SUM and COUNT words per row) timed on a plain table
+        words = 2
+        pk_ms = ctx.atomic_peak(args.groups, words, rows)
+        line["atomics"] = {"achieved": rows / (dom_ms / 1000.0), "peak": rows / (pk_ms / 1000.0),
+                           "unit": "slot updates/s", "frac": pk_ms / dom_ms,
+                           "peak_source": f"pv_atomic_peak: {rows} uniform random updates of {words} words "
+                                          f"into {args.groups} slots, measured in this run"}
     if rank == 0 and not args.no_cpu_baseline:
-        rate, cores, n = cpu_oracle_rate(plan, tables, args.cpu_budget, rows)
+        rate, cores, n = cpu_oracle_rate(plan, tables, args.cpu_budget, rows, args.cpu_threads)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"the whole {rows}-row table, {n} runs on {cores} threads"}
     if rank == 0:
@@ -484,6 +544,9 @@ def main():
     ap.add_argument("--build-ht", default="perfect")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--hot-l2", action="store_true",
+                    help="no L2 flush between steps (hot-L2 numbers, labelled as such)")
+    ap.add_argument("--cpu-threads", type=int, default=0, help="oracle threads (0 = all host cores)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

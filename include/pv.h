@@ -256,6 +256,14 @@ pv_status pv_last_launch_count(pv_ctx* ctx, int32_t* n);
  * ms[0..max), and their count into *n.  Not recorded inside graph capture. */
 pv_status pv_set_kernel_timing(pv_ctx* ctx, int32_t enable);
 pv_status pv_kernel_times(pv_ctx* ctx, float* ms, int32_t max, int32_t* n);
+/* Measured random-atomic throughput, the roofline of global aggregation
+ * tables that outgrow L2 (Section 9.2.2 aggregation with many groups): a
+ * ctx-allocated table of `slots` x `words` zeroed 64-bit words receives
+ * n_updates updates, each adding 1 with atomicAdd to every word of one
+ * uniformly hashed slot.  One warm-up pass, an L2 flush, then one timed pass;
+ * *ms = its duration from CUDA events.  Synchronises; allocates and frees the
+ * table; not capturable.  words in 1..16; the table is at most 64 GB. */
+pv_status pv_atomic_peak(pv_ctx* ctx, int64_t slots, int32_t words, int64_t n_updates, float* ms);
 /* Enqueues one kernel that busy-waits for `ns` nanoseconds of GPU clock
  * (bounded; for exercising the pv_sync watchdog). */
 pv_status pv_debug_spin(pv_ctx* ctx, int64_t ns);

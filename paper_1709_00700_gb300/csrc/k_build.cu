@@ -133,6 +133,19 @@ __global__ void k_cuckoo_dupcheck(const __grid_constant__ DevHT h, int32_t* err)
   }
 }
 
+// Presence bits of a perfect array: word w holds slots 32w .. 32w+31 (bit j
+// set when slot 32w + j is occupied), one warp ballot per word.
+__global__ void k_perfect_bits(const uint64_t* slots, int64_t cap, uint32_t* bits) {
+  const int64_t words = (cap + 31) / 32;
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t w = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; w < words; w += nwarps) {
+    const int64_t i = w * 32 + lane;
+    const uint32_t b = __ballot_sync(0xffffffffu, i < cap && slots[i] != 0);
+    if (lane == 0) bits[w] = b;
+  }
+}
+
 pv_status build_table(const BuildEnv& env, const BuildInput& in, const pv_ht_variant& var, int64_t kmin,
                       int64_t kmax, BuildTable& out, std::string& msg) {
   DevHT& h = out.ht;
@@ -182,13 +195,18 @@ pv_status build_table(const BuildEnv& env, const BuildInput& in, const pv_ht_var
   }
   const int max_ev = var.max_evictions > 0 ? var.max_evictions : 32 * std::max(1, h.log2cap);
   out.n_payload = in.n_payload;
-  out.mem = env.alloc(bytes + 64, env.user);
+  // [slots | 16-byte stats | presence bits (perfect arrays without payload)]
+  const size_t stats_off = (bytes + 15) & ~size_t(15);
+  const bool with_bits = var.kind == PV_HT_PERFECT && in.n_payload == 0;
+  const size_t bits_bytes = with_bits ? static_cast<size_t>((h.cap + 31) / 32) * 4 : 0;
+  out.mem = env.alloc(stats_off + 16 + bits_bytes + 64, env.user);
   if (!out.mem) {
     msg = "allocator returned NULL";
     return PV_ERR_OOM;
   }
   h.slots = static_cast<uint64_t*>(out.mem);
-  unsigned long long* stats = reinterpret_cast<unsigned long long*>(static_cast<char*>(out.mem) + ((bytes + 15) & ~size_t(15)));
+  unsigned long long* stats = reinterpret_cast<unsigned long long*>(static_cast<char*>(out.mem) + stats_off);
+  h.bits = with_bits ? reinterpret_cast<const uint32_t*>(static_cast<char*>(out.mem) + stats_off + 16) : nullptr;
   out.slot_bytes = bytes;
   BuildParams& bp = out.bp;
   bp = BuildParams{};
@@ -237,6 +255,12 @@ pv_status rebuild_table(const BuildEnv& env, const BuildTable& t) {
       k_cuckoo_dupcheck<<<g2, 256, 0, env.stream>>>(h, env.err);
       ++*env.launches;
     }
+  }
+  if (h.bits != nullptr) {
+    const int64_t words = (h.cap + 31) / 32;
+    const int g3 = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(env.sm_count * 8, (words + 7) / 8)));
+    k_perfect_bits<<<g3, 256, 0, env.stream>>>(h.slots, h.cap, const_cast<uint32_t*>(h.bits));
+    ++*env.launches;
   }
   return cudaGetLastError() == cudaSuccess ? PV_OK : PV_ERR_CUDA;
 }

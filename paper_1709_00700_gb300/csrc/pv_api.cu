@@ -432,6 +432,18 @@ __global__ void k_discard(char* p, int64_t bytes) {
     asm volatile("discard.global.L2 [%0], 128;" ::"l"(p + i) : "memory");
 }
 
+// Random-slot atomic throughput (measurement support).  Update u adds 1 to
+// each of the `words` 64-bit words of slot floor(fmix64(u ^ seed) * slots /
+// 2^64) with atomicAdd: the access pattern of a global aggregation table whose
+// groups are spread uniformly.
+__global__ void k_atomic_rand(unsigned long long* t, int64_t slots, int words, int64_t n, uint64_t seed) {
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t s = __umul64hi(fmix64(static_cast<uint64_t>(u) ^ seed), static_cast<uint64_t>(slots));
+    unsigned long long* p = t + s * static_cast<uint64_t>(words);
+    for (int w = 0; w < words; ++w) atomicAdd(p + w, 1ull);
+  }
+}
+
 __global__ void k_spin(int64_t ns) {
   uint64_t t0, t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
@@ -1046,6 +1058,42 @@ pv_status pv_mlp_adam(pv_ctx* c, float* params, const float* grad, float* m, flo
   c->launches = 0;
   pv_status s = mlp_adam(c->stream, &c->launches, params, grad, m, v, n, lr, beta1, beta2, eps, step);
   return s == PV_OK ? s : fail(c, s, "pv_mlp_adam failed");
+}
+
+pv_status pv_atomic_peak(pv_ctx* c, int64_t slots, int32_t words, int64_t n_updates, float* ms) {
+  if (!c || !ms || slots < 1 || words < 1 || words > 16 || n_updates < 1) return PV_ERR_INVALID_ARG;
+  if (c->capturing) return fail(c, PV_ERR_INVALID_ARG, "pv_atomic_peak cannot be captured");
+  const size_t bytes = static_cast<size_t>(slots) * static_cast<size_t>(words) * 8;
+  if (bytes > (size_t{64} << 30)) return fail(c, PV_ERR_INVALID_ARG, "table larger than 64 GB");
+  pv_status st = pv_l2_flush(c);  // allocates the flush buffer before the table
+  if (st != PV_OK) return st;
+  auto* t = static_cast<unsigned long long*>(dalloc(c, bytes));
+  if (!t) return fail(c, PV_ERR_OOM, "allocator returned NULL");
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(t, 0, bytes, c->stream);
+  const int grid = c->sm_count * 8;
+  if (ce == cudaSuccess) {
+    k_atomic_rand<<<grid, 256, 0, c->stream>>>(t, slots, words, n_updates, 0x9e3779b97f4a7c15ull);  // warm-up
+    ce = cudaGetLastError();
+  }
+  if (ce == cudaSuccess) st = pv_l2_flush(c);
+  if (ce == cudaSuccess && st == PV_OK) ce = cudaEventRecord(e0, c->stream);
+  if (ce == cudaSuccess && st == PV_OK) {
+    k_atomic_rand<<<grid, 256, 0, c->stream>>>(t, slots, words, n_updates, 0x2545f4914f6cdd1dull);
+    ce = cudaGetLastError();
+  }
+  if (ce == cudaSuccess && st == PV_OK) ce = cudaEventRecord(e1, c->stream);
+  if (ce == cudaSuccess && st == PV_OK) ce = cudaEventSynchronize(e1);
+  if (ce == cudaSuccess && st == PV_OK) ce = cudaEventElapsedTime(ms, e0, e1);
+  cudaStreamSynchronize(c->stream);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  dfree(c, t);
+  if (st != PV_OK) return st;
+  if (ce != cudaSuccess) return fail(c, PV_ERR_CUDA, cudaGetErrorString(ce));
+  return PV_OK;
 }
 
 pv_status pv_debug_spin(pv_ctx* c, int64_t ns) {

@@ -32,6 +32,7 @@ constexpr uint32_t kEmpty32 = 0xFFFFFFFFu;
 // Perfect: slot (key - kmin) holds (payload << 32) | 1, 0 when empty.
 struct DevHT {
   uint64_t* slots;
+  const uint32_t* bits;  // perfect array without payload: presence bit per slot (probes read these), else null
   int32_t kind;      // pv_ht_kind
   int32_t hash;      // pv_hash_fn
   int32_t log2cap;
@@ -300,6 +301,10 @@ __device__ __forceinline__ bool probe_key(const DevHT& h, int64_t key, int32_t& 
   if (h.kind == PV_HT_PERFECT) {
     const int64_t i = key - h.kmin;
     if (static_cast<uint64_t>(i) >= static_cast<uint64_t>(h.cap)) return false;
+    if (h.bits != nullptr) {  // 1 bit per key instead of 8 bytes: small enough to stay in L1
+      pay = 0;
+      return (__ldg(h.bits + (i >> 5)) >> (i & 31)) & 1u;
+    }
     const uint64_t s = __ldg(reinterpret_cast<const unsigned long long*>(h.slots) + i);
     pay = static_cast<int32_t>(s >> 32);
     return s != 0;

@@ -122,6 +122,8 @@ _SIGS = {
     "pv_mlp_adam": (ctypes.c_int32, [ctypes.c_void_p] + [ctypes.c_void_p] * 4 + [ctypes.c_int64, ctypes.c_float,
                                                                                  ctypes.c_float, ctypes.c_float,
                                                                                  ctypes.c_float, ctypes.c_int32]),
+    "pv_atomic_peak": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64,
+                                        ctypes.POINTER(ctypes.c_float)]),
     "pv_filter_project_noalloc": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                                    ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
@@ -245,6 +247,12 @@ class Context:
 
     def set_kernel_timing(self, on: bool):
         self._check(self.lib.pv_set_kernel_timing(self.h, 1 if on else 0))
+
+    def atomic_peak(self, slots: int, words: int, n_updates: int) -> float:
+        """Milliseconds of n_updates random-slot updates (pv_atomic_peak)."""
+        ms = ctypes.c_float()
+        self._check(self.lib.pv_atomic_peak(self.h, slots, words, n_updates, ctypes.byref(ms)))
+        return float(ms.value)
 
     def kernel_times(self) -> list:
         buf = (ctypes.c_float * 64)()
