@@ -179,6 +179,7 @@ pv_status build_table(const BuildEnv& env, const BuildInput& in, const pv_ht_var
     h.cap = span;
     h.kmin = kmin;
     h.log2cap = 0;
+    h.narrow = kmin >= INT32_MIN && kmin + span <= (int64_t(1) << 31) ? 1 : 0;
     bytes = static_cast<size_t>(span) * 8;
   } else {
     const double lf = var.load_factor > 0 && var.load_factor <= 1 ? var.load_factor : 0.5;

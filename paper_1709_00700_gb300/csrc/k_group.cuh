@@ -498,8 +498,15 @@ template <class S> struct SinkPipelined<S, std::void_t<decltype(S::kPipelined)>>
   static constexpr bool value = S::kPipelined;
 };
 
+// Branched kernels of small shapes (at most two aggregates) are held to 64
+// registers, so two 512-thread CTAs share an SM: they are latency-bound
+// (lazy loads and probes), and occupancy hides the latency.
+template <class SH, class Sink, bool PRED> struct GroupRegs {
+  static constexpr int value = !PRED && SH::Aggs::N <= 2 ? 64 : SinkRegs<Sink>::value;
+};
+
 template <class SH, bool PRED, bool CHUNK, int U, class Sink>
-__global__ void __maxnreg__(SinkRegs<Sink>::value) k_group(const __grid_constant__ KParams kp, const __grid_constant__ GroupDesc gd, const __grid_constant__ GroupOut g) {
+__global__ void __maxnreg__((GroupRegs<SH, Sink, PRED>::value)) k_group(const __grid_constant__ KParams kp, const __grid_constant__ GroupDesc gd, const __grid_constant__ GroupOut g) {
   extern __shared__ unsigned long long smem[];
   if (blockIdx.x == 0 && threadIdx.x == 0) *g.out_count = 0;  // extraction runs after this kernel
   Sink sink(gd, g, kp.err, smem);
@@ -533,7 +540,7 @@ __global__ void __maxnreg__(SinkRegs<Sink>::value) k_group(const __grid_constant
       consume(it);
     });
   } else {
-    for_items<CHUNK, U>(kp.n_items, [&](const int64_t (&idx)[U]) {
+    for_items_pf<SH, CHUNK, U, first_stage_slots<SH>()>(kp, [&](const int64_t (&idx)[U]) {
       Item<SH> it[U];
       eval_items<SH, PRED, U>(it, kp, idx);
       consume(it);

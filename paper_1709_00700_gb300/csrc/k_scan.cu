@@ -53,7 +53,7 @@ __global__ void __maxnreg__(128) k_aggregate(const __grid_constant__ KParams kp,
   if constexpr (PRED) {
     for_items_pipelined<SH, CHUNK, U>(kp, consume);
   } else {
-    for_items_pf<SH, CHUNK, U>(kp, [&](const int64_t (&idx)[U]) {
+    for_items_pf<SH, CHUNK, U, first_stage_slots<SH>()>(kp, [&](const int64_t (&idx)[U]) {
       Item<SH> it[U];
       eval_items<SH, PRED, U>(it, kp, idx);
       consume(it);

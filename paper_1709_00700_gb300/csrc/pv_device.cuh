@@ -37,6 +37,7 @@ struct DevHT {
   int32_t hash;      // pv_hash_fn
   int32_t log2cap;
   int32_t k;         // cuckoo functions
+  int32_t narrow;    // perfect: kmin >= INT32_MIN and kmin + cap <= 2^31, so 32-bit keys index in 32 bits
   int64_t cap;       // slots (power of two for linear/cuckoo; domain size for perfect)
   int64_t kmin;      // perfect: smallest key
   uint64_t seed[4];  // per-function hash seeds
@@ -336,6 +337,81 @@ __device__ __forceinline__ bool probe_key(const DevHT& h, int64_t key, int32_t& 
   return false;
 }
 
+// HASH_PROBE of the 4 rows of an item; returns the mask with the misses
+// cleared and binds each hit's payload (0 for a miss).  Perfect tables
+// (the kind is the same for every lane) probe all 4 rows without branches:
+// 4 independent read-only loads, a dead row of a live item costing one cache
+// hit.  Hashed tables probe the live rows (every row when all_rows) one at a
+// time, as their probe sequences differ.
+template <class T>
+__device__ __forceinline__ uint32_t probe_item(const DevHT& h, const T (&fk)[4], uint32_t mask, int32_t (&pay)[4],
+                                               bool all_rows) {
+  if (h.kind == PV_HT_PERFECT) {
+    uint32_t hit = 0;
+    if constexpr (sizeof(T) <= 4) {
+      // Domain inside int32: (fk - kmin) mod 2^32 < cap exactly when kmin <= fk < kmin + cap
+      // (a wrapped difference would need fk < INT32_MIN or kmin + cap > 2^31).
+      if (h.narrow) {
+        const uint32_t k0 = static_cast<uint32_t>(h.kmin), cap = static_cast<uint32_t>(h.cap);
+        if (h.bits != nullptr) {
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const uint32_t i = static_cast<uint32_t>(static_cast<int32_t>(fk[r])) - k0;
+            const bool in = i < cap;
+            const uint32_t ic = in ? i : 0u;
+            const uint32_t w = __ldg(h.bits + (ic >> 5));
+            hit |= static_cast<uint32_t>(in & ((w >> (ic & 31u)) & 1u)) << r;
+            pay[r] = 0;
+          }
+        } else {
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const uint32_t i = static_cast<uint32_t>(static_cast<int32_t>(fk[r])) - k0;
+            const bool in = i < cap;
+            const uint64_t sv = __ldg(reinterpret_cast<const unsigned long long*>(h.slots) + (in ? i : 0u));
+            const bool ok = in && sv != 0;
+            hit |= static_cast<uint32_t>(ok) << r;
+            pay[r] = ok ? static_cast<int32_t>(sv >> 32) : 0;
+          }
+        }
+        return mask & hit;
+      }
+    }
+    if (h.bits != nullptr) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const uint64_t i = static_cast<uint64_t>(static_cast<int64_t>(fk[r]) - h.kmin);
+        const bool in = i < static_cast<uint64_t>(h.cap);
+        const uint64_t ic = in ? i : 0;
+        const uint32_t w = __ldg(h.bits + (ic >> 5));
+        hit |= static_cast<uint32_t>(in && ((w >> (ic & 31)) & 1u)) << r;
+        pay[r] = 0;
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const uint64_t i = static_cast<uint64_t>(static_cast<int64_t>(fk[r]) - h.kmin);
+        const bool in = i < static_cast<uint64_t>(h.cap);
+        const uint64_t sv = __ldg(reinterpret_cast<const unsigned long long*>(h.slots) + (in ? i : 0));
+        const bool ok = in && sv != 0;
+        hit |= static_cast<uint32_t>(ok) << r;
+        pay[r] = ok ? static_cast<int32_t>(sv >> 32) : 0;
+      }
+    }
+    return mask & hit;
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    pay[r] = 0;
+    if (all_rows || ((mask >> r) & 1u)) {
+      int32_t p = 0;
+      if (probe_key(h, static_cast<int64_t>(fk[r]), p)) pay[r] = p;
+      else mask &= ~(1u << r);
+    }
+  }
+  return mask;
+}
+
 // LOOP body up to the sink: FILTER, then HASH_PROBE in order, then loads of
 // the columns the sink needs.  Branched mode (PRED = false) evaluates one
 // operation at a time and skips the loads and probes of an item whose rows
@@ -369,17 +445,7 @@ __device__ __forceinline__ void eval_item(Item<SH>& it, const KParams& kp, int64
     constexpr int S = JP::slot_of[J];
     if (PRED || it.mask) {
       if constexpr (!PRED && !((W::slots >> S) & 1u)) load_slots<SH, (1u << S)>(it, kp, item);
-      auto& fk = VGet<S>::get(it.v);
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        it.pay[J][r] = 0;
-        if (PRED || ((it.mask >> r) & 1u)) {
-          int32_t p = 0;
-          const bool hit = probe_key(kp.probe[J], static_cast<int64_t>(fk[r]), p);
-          it.pay[J][r] = p;
-          if (!hit) it.mask &= ~(1u << r);
-        }
-      }
+      it.mask = probe_item(kp.probe[J], VGet<S>::get(it.v), it.mask, it.pay[J], PRED);
     }
   });
   if constexpr (!PRED) {

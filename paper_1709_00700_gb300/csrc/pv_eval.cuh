@@ -50,19 +50,8 @@ __device__ __forceinline__ void eval_items(Item<SH> (&it)[U], const KParams& kp,
         if (it[u].mask) load_slots<SH, (1u << S)>(it[u], kp, idx[u]);
     }
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      auto& fk = VGet<S>::get(it[u].v);
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        it[u].pay[J][r] = 0;
-        if (PRED || ((it[u].mask >> r) & 1u)) {
-          int32_t p = 0;
-          const bool hit = probe_key(kp.probe[J], static_cast<int64_t>(fk[r]), p);
-          it[u].pay[J][r] = p;
-          if (!hit) it[u].mask &= ~(1u << r);
-        }
-      }
-    }
+    for (int u = 0; u < U; ++u)
+      if (PRED || it[u].mask) it[u].mask = probe_item(kp.probe[J], VGet<S>::get(it[u].v), it[u].mask, it[u].pay[J], PRED);
   });
   if constexpr (!PRED) {
 #pragma unroll
@@ -124,16 +113,7 @@ __device__ __forceinline__ void filter_probe_items(Item<SH> (&it)[U], const KPar
     constexpr int J = decltype(j)::value;
     constexpr int S = JP::slot_of[J];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      auto& fk = VGet<S>::get(it[u].v);
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        int32_t p = 0;
-        const bool hit = probe_key(kp.probe[J], static_cast<int64_t>(fk[r]), p);
-        it[u].pay[J][r] = p;
-        if (!hit) it[u].mask &= ~(1u << r);
-      }
-    }
+    for (int u = 0; u < U; ++u) it[u].mask = probe_item(kp.probe[J], VGet<S>::get(it[u].v), it[u].mask, it[u].pay[J], true);
   });
 }
 
@@ -155,13 +135,13 @@ template <class... Ts> struct ItemShifts<TList<Ts...>> {
 // lanes: lane c prefetches column c.  Only whole in-range chunks are
 // prefetched (16-byte aligned: column bases are 16-byte aligned and 128 rows
 // of any column type are a multiple of 16 bytes).
-template <class SH>
+template <class SH, uint32_t MASK = ~0u>
 struct LanePrefetch {
   static_assert(SH::Cols::N <= 16, "one lane per column, 4-bit shifts");
   const char* base = nullptr;
   uint32_t shift = 0;
   __device__ __forceinline__ LanePrefetch(const KParams& kp, int lane) {
-    if (lane < SH::Cols::N) {
+    if (lane < SH::Cols::N && ((MASK >> lane) & 1u)) {
       base = static_cast<const char*>(kp.col[lane]);
       shift = static_cast<uint32_t>(ItemShifts<typename SH::Cols::L>::value >> (4 * lane)) & 15u;
     }
@@ -175,10 +155,20 @@ struct LanePrefetch {
   }
 };
 
+// Columns a branched pipeline reads for every item, before its first branch:
+// the filter columns, else the first probe's key column, else all of them.
+// Prefetching the others would fetch sectors the lazy loads skip.
+template <class SH>
+constexpr uint32_t first_stage_slots() {
+  if constexpr (SH::Where::N > 0) return SH::Where::slots;
+  else if constexpr (SH::Probes::N > 0) return 1u << SH::Probes::slot_of[0];
+  else return ~0u;
+}
+
 // Grid-stride item loop (as for_items) that also bulk-prefetches into L2
-// the chunk its warp will read kp.prefetch trips later.  Chunked access: no
-// prefetch.
-template <class SH, bool CHUNK, int U, class F>
+// the chunk of the MASK columns its warp will read kp.prefetch trips later.
+// Chunked access: no prefetch.
+template <class SH, bool CHUNK, int U, uint32_t MASK = ~0u, class F>
 __device__ __forceinline__ void for_items_pf(const KParams& kp, F&& f) {
   const int pf = CHUNK ? 0 : kp.prefetch;
   if (pf == 0) {
@@ -189,7 +179,7 @@ __device__ __forceinline__ void for_items_pf(const KParams& kp, F&& f) {
   const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const int64_t n_full = kp.n_rows >> 2;
-  const LanePrefetch<SH> lp(kp, lane);
+  const LanePrefetch<SH, MASK> lp(kp, lane);
   auto prefetch = [&](int64_t k) {
 #pragma unroll
     for (int u = 0; u < U; ++u) lp.issue((t - lane) + (k * U + u) * T, n_full);

@@ -401,3 +401,36 @@ def test_rebuild_after_in_place_change_and_in_a_graph(ctx):
         ctx.free(res)
         for h in hts:
             ctx.free(h)
+
+
+@pytest.mark.parametrize("dim_keys", [
+    np.arange(-2**31, -2**31 + 40, dtype=np.int64).astype(np.int32),          # domain at the bottom of int32
+    np.arange(-20, 20, dtype=np.int32),                                      # domain straddling zero
+    np.arange(2**31 - 40, 2**31, dtype=np.int64).astype(np.int32),           # domain at the top of int32
+])
+def test_perfect_probe_domain_edges(ctx, dim_keys):
+    D = len(dim_keys)
+    dim = {"key": dim_keys, "f": (np.arange(D) % 3).astype(np.int32)}
+    extremes = np.array([-2**31, -2**31 + 1, 2**31 - 1, 2**31 - 2, 0, -1, 1], dtype=np.int64)
+    fk = np.concatenate([extremes, np.asarray(dim_keys, dtype=np.int64)[::3],
+                         np.asarray(dim_keys, dtype=np.int64)[:7] - 2**32 + 2**31]).astype(np.int64)
+    fk = fk[(fk >= -2**31) & (fk < 2**31)].astype(np.int32)
+    fact = {"fk": np.tile(fk, 5)}
+    register(ctx, {"edim": dim, "efact": fact})
+    plan = {"fact": "efact", "builds": [{"table": "edim", "key": "key", "filters": [["f", "lt", 2]], "payload": []}],
+            "probes": [{"build": 0, "fk": "fk"}], "aggs": [["count"]]}
+    w = want(plan, {"edim": dim, "efact": fact})
+    for kind in ("perfect", "linear", "cuckoo"):
+        for pred in ("branch", "predicated"):
+            got = ctx.query(plan, pv.variant(pred=pred), pv.ht_variant(kind))
+            assert_same(got, w, ctxmsg=f"{kind} {pred}")
+
+
+def test_int64_build_keys_are_unsupported(ctx):
+    dim = {"key": np.arange(2**31 - 5, 2**31 + 5, dtype=np.int64), "f": np.zeros(10, dtype=np.int32)}
+    register(ctx, {"i64dim": dim, "i64fact": {"fk": np.arange(10, dtype=np.int32)}})
+    plan = {"fact": "i64fact", "builds": [{"table": "i64dim", "key": "key", "filters": [], "payload": []}],
+            "probes": [{"build": 0, "fk": "fk"}], "aggs": [["count"]]}
+    with pytest.raises(pv.PVError) as e:
+        ctx.query(plan, pv.variant(), pv.ht_variant("perfect"))
+    assert e.value.status == -2
