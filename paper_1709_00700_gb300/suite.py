@@ -251,11 +251,11 @@ def algorithm1_config(train: list, timings: dict, grid: list, q_sweeps: int = 3,
 
 
 def explore(ctx: "pv.Context", n_queries: int = 500, max_rows: int = 300_000_000, min_rows: int = 1_000_000,
-            seed: int = 1709, reps: int = 3, log=print) -> dict:
+            seed: int = 1709, reps: int = 3, log=print, data: "SuiteData | None" = None) -> dict:
     """Statistics and exhaustive timings of every query of the suite."""
     t0 = time.time()
     queries = make_queries(n_queries, seed, min_rows, max_rows)
-    data = SuiteData(ctx, max_rows)
+    data = data or SuiteData(ctx, max_rows)
     stats, timings = {}, {}
     for i, q in enumerate(queries):
         stats[q["id"]] = data.stats(q)
@@ -366,6 +366,50 @@ def judge(ctx: "pv.Context", ex: dict, n_train: int | None = None, candidates=CA
     }
 
 
+def confirm(data: SuiteData, ex: dict, summary: dict, reps: int = 15, top: int = 3, log=print) -> dict:
+    """Re-times, for every held-out query, the exploration's `top` fastest
+    variants, the network's pick and the Algorithm 1 configuration with the
+    median of `reps` cold-L2 runs each, and judges the pick and the
+    configuration against the fastest of them.  The exploration's own best is
+    the minimum of many 3-run medians (biased low by selection) and, for
+    queries of tens of microseconds, of times quantised by the event timer;
+    re-timing the candidates removes both effects from the judgement."""
+    t0 = time.time()
+    qmap = {q["id"]: q for q in ex["queries"]}
+    rows = []
+    for n, p in enumerate(summary["per_query"]):
+        q = qmap[p["id"]]
+        g = grid_key(q)
+        tm = ex["timings"][q["id"]]
+        finite = sorted((v for v in GRIDS[g] if math.isfinite(tm[autotune.variant_key(v)])),
+                        key=lambda v: tm[autotune.variant_key(v)])
+        cands = {}
+        for v in finite[:top] + [p["pick"], summary["alg1_configs"][g]]:
+            cands.setdefault(autotune.variant_key(v), v)
+        plan = data.prepare(q)
+        med = {}
+        for bk in sorted({v.get("build", "") for v in cands.values()}):
+            m = autotune.Measurer(data.ctx, plan, build_ht=bk or "perfect", reps=reps, cap_factor=math.inf)
+            for k, v in cands.items():
+                if v.get("build", "") == bk:
+                    med[k] = m({kk: x for kk, x in v.items() if kk != "build"})
+            m.close()
+        best = min(med.values())
+        rows.append({"id": q["id"], "family": g, "best_ms": best,
+                     "pick_ratio": med[autotune.variant_key(p["pick"])] / best,
+                     "config_ratio": med[autotune.variant_key(summary["alg1_configs"][g])] / best})
+        if log and (n % 25 == 0 or n == len(summary["per_query"]) - 1):
+            log(f"  confirmed {n + 1}/{len(summary['per_query'])} queries, {time.time() - t0:.0f}s")
+    rp = np.array([r["pick_ratio"] for r in rows])
+    rc = np.array([r["config_ratio"] for r in rows])
+    gm = lambda r: float(np.exp(np.mean(np.log(np.minimum(r, 1e6)))))  # noqa: E731
+    return {"reps": reps, "candidates": f"the exploration's {top} fastest, the pick, the Algorithm 1 configuration",
+            "mlp_within_10pct": float(np.mean(rp <= 1.10)), "mlp_geomean_slowdown": gm(rp),
+            "mlp_worst_slowdown": float(rp.max()), "alg1_within_10pct": float(np.mean(rc <= 1.10)),
+            "alg1_geomean_slowdown": gm(rc), "alg1_worst_slowdown": float(rc.max()), "seconds": time.time() - t0,
+            "per_query": rows}
+
+
 def run(ctx: "pv.Context", n_queries: int = 500, max_rows: int = 300_000_000, min_rows: int = 1_000_000,
         n_train: int | None = None, seed: int = 1709, reps: int = 3, candidates=CANDIDATES, log=print) -> dict:
     ex = explore(ctx, n_queries, max_rows, min_rows, seed, reps, log)
@@ -386,25 +430,32 @@ def main(argv=None):
     ap.add_argument("--timings-out", default="")
     ap.add_argument("--out", default="")
     ap.add_argument("--graphs", action="store_true", help="run the CUDA-graph batch experiment only")
+    ap.add_argument("--confirm-reps", type=int, default=15, help="re-timing runs per candidate (0 = skip)")
     a = ap.parse_args(argv)
     ctx = pv.Context(0)
     if a.graphs:
         print(json.dumps(graph_experiment(ctx)))
         ctx.close()
         return
+    data = None
     if a.timings_in:
         with open(a.timings_in) as f:
             ex = json.load(f)
         ex["stats"] = {int(k): v for k, v in ex["stats"].items()}
         ex["timings"] = {int(k): v for k, v in ex["timings"].items()}
     else:
-        ex = explore(ctx, a.queries, a.max_rows, a.min_rows, reps=a.reps)
+        data = SuiteData(ctx, a.max_rows)
+        ex = explore(ctx, a.queries, a.max_rows, a.min_rows, reps=a.reps, data=data)
         if a.timings_out:
             with open(a.timings_out, "w") as f:
                 json.dump(ex, f)
     cands = ((a.epochs, a.ensemble, a.lr),) if a.epochs else CANDIDATES
     summary = judge(ctx, ex, candidates=cands)
-    print(json.dumps({k: v for k, v in summary.items() if k != "per_query"}))
+    if a.confirm_reps > 0:
+        data = data or SuiteData(ctx, a.max_rows)
+        summary["confirmed"] = confirm(data, ex, summary, reps=a.confirm_reps)
+    print(json.dumps({k: (v if k != "confirmed" else {kk: vv for kk, vv in v.items() if kk != "per_query"})
+                      for k, v in summary.items() if k != "per_query"}))
     if a.out:
         with open(a.out, "w") as f:
             json.dump(summary, f)

@@ -24,3 +24,16 @@ def test_small_suite_runs_and_picks_from_the_grid():
         assert p["best_ms"] <= p["pick_ms"] and p["best_ms"] <= p["config_ms"]
         assert math.isfinite(p["pick_ms"])
     assert 0.0 <= s["mlp_within_10pct"] <= 1.0
+
+
+def test_confirm_retimes_the_held_out_candidates():
+    ctx = pv.Context(0)
+    data = suite.SuiteData(ctx, 2_000_000)
+    ex = suite.explore(ctx, 12, 2_000_000, 200_000, reps=2, log=None, data=data)
+    s = suite.judge(ctx, ex, candidates=((200, 1, 3e-3),))
+    c = suite.confirm(data, ex, s, reps=3, log=None)
+    ctx.close()
+    assert c["reps"] == 3 and len(c["per_query"]) == len(s["per_query"])
+    for r in c["per_query"]:
+        assert r["pick_ratio"] >= 1.0 and r["config_ratio"] >= 1.0 and math.isfinite(r["pick_ratio"])
+    assert 0.0 <= c["mlp_within_10pct"] <= 1.0
