@@ -153,8 +153,12 @@ typedef struct {
   int32_t items_per_thread;  /* unroll: 4-row items per thread per trip, 1, 2 or 4 (0 = 2) */
   int32_t threads_per_table; /* PV_AGG_LOCAL: 1 = thread-private tables, 0 = one per CTA */
   int32_t cuckoo_k;          /* aggregation cuckoo hash functions (0 = 3) */
-  int32_t prefetch;          /* grid-stride predicated pipelines: bulk-prefetch each warp's column
-                                chunks this many loop trips ahead into L2 (0 = off) */
+  int32_t prefetch;          /* grid-stride pipelines: bulk-prefetch each warp's column chunks this
+                                many loop trips ahead into L2 (0 = off) */
+  int32_t warp_agg;          /* HASH_AGGREGATE with atomic tables (local or global, not thread-private):
+                                1 = lanes of a warp holding the same group key first combine their
+                                aggregates (match_any), one lane updates the table (Section 4's local
+                                pre-aggregation applied within a warp); 0 = every row updates */
   uint64_t seed;             /* aggregation hash seeds */
 } pv_variant;
 

@@ -30,10 +30,10 @@ FAMILIES = ("filter", "grouped", "star")
 PLAN_FEATURES = ("log_rows", "sel", "log_sel", "log_groups", "log_groups_per_row", "top_share", "n_preds",
                  "n_probes", "log_dim_rows", "bytes_in", "bytes_out", "n_aggs", "project", "log_bytes",
                  "log_out_rows", "fam_filter", "fam_grouped", "fam_star", "log_hot_rows", "log_groups_hit",
-                 "log_rows_per_group")
+                 "log_rows_per_group", "log_collision", "warp_repeats")
 VARIANT_FEATURES = ("multi", "local", "ht_linear", "ht_cuckoo", "ht_perfect", "multshift", "predicated",
                     "chunked", "log_block", "grid_mult", "unroll", "private_tables", "prefetch", "build_linear",
-                    "build_cuckoo", "build_perfect")
+                    "build_cuckoo", "build_perfect", "warp_agg")
 N_FEATURES = len(PLAN_FEATURES) + len(VARIANT_FEATURES)
 
 
@@ -46,6 +46,8 @@ def plan_vector(st: dict) -> list:
     sel = min(1.0, max(float(st["sel"]), 1e-6))
     groups = max(1.0, float(st.get("groups", 1)))
     fam = st["family"]
+    # without a measured collision probability: uniform over the groups, or one group when filtering
+    coll = float(st["collision"]) if "collision" in st else (1.0 if fam == "filter" else 1.0 / groups)
     return [math.log10(rows), sel, math.log10(sel), math.log10(groups), math.log10(groups / rows),
             float(st.get("top_share", 0.0)), float(st.get("n_preds", 0)), float(st.get("n_probes", 0)),
             math.log10(1.0 + float(st.get("dim_rows", 0))), float(st.get("bytes_in", 0)),
@@ -55,7 +57,10 @@ def plan_vector(st: dict) -> list:
             # contention proxies: rows of the hottest group, groups touched, rows per touched group
             math.log10(1.0 + rows * sel * float(st.get("top_share", 0.0))),
             math.log10(max(1.0, min(groups, rows * sel))),
-            math.log10(max(1.0, rows * sel / max(1.0, min(groups, rows * sel))))]
+            math.log10(max(1.0, rows * sel / max(1.0, min(groups, rows * sel)))),
+            # key repeats: probability that two surviving rows share a group, and the expected
+            # number of other rows of a 32-row warp step holding the same key
+            math.log10(max(coll, 1e-9)), min(31.0, 31.0 * coll)]
 
 
 def variant_vector(v: dict) -> list:
@@ -66,7 +71,7 @@ def variant_vector(v: dict) -> list:
             float(v.get("pred") == "predicated"), float(v.get("access") == "chunked"),
             math.log2(v.get("block", 256)), float(v.get("grid_mult", 0)), float(v.get("items_per_thread", 2)),
             float(v.get("threads_per_table", 0) == 1), float(v.get("prefetch", 0)), float(b == "linear"),
-            float(b == "cuckoo"), float(b == "perfect")]
+            float(b == "cuckoo"), float(b == "perfect"), float(v.get("warp_agg", 0))]
 
 
 def features(stats: dict, variant: dict) -> np.ndarray:

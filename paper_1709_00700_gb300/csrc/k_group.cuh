@@ -172,6 +172,41 @@ __device__ __forceinline__ uint64_t global_slot(const GroupOut& g, uint64_t key,
   else return global_lookup<PV_HT_CUCKOO>(g, key, err);
 }
 
+// Warp pre-aggregation of the atomic sinks (variant flag warp_agg): the
+// active lanes holding the same group key combine their accumulator codes,
+// and the group's lowest lane alone updates the table.  The lanes of a group
+// form a list in lane order; pointer jumping (each step adds the successor's
+// partial and skips to the successor's successor) leaves the whole group's
+// combination in its first lane after ceil(log2(group size)) steps.  One
+// ballot skips all of it when no key repeats within the warp.  Returns
+// whether this lane still updates the table.
+template <class SH>
+__device__ __forceinline__ bool warp_preaggregate(uint64_t key, uint64_t (&c)[SH::Aggs::N + 1]) {
+  constexpr int NA = SH::Aggs::N;
+  const unsigned active = __activemask();
+  const unsigned peers = __match_any_sync(active, static_cast<unsigned long long>(key));
+  const int lane = threadIdx.x & 31;
+  const unsigned after = peers & ~((2u << lane) - 1u);  // lane 31: 2u << 31 == 0, nothing after
+  if (__ballot_sync(active, after != 0u) == 0u) return true;
+  int nxt = after ? __ffs(after) - 1 : lane;
+  int more = after != 0u;
+  while (__any_sync(active, more)) {
+    static_for<NA + 1>([&](auto a) {
+      constexpr int I = decltype(a)::value;
+      constexpr int F = I < NA ? SH::Aggs::func_of[I < NA ? I : 0] : PV_COUNT;
+      const uint64_t o = __shfl_sync(active, static_cast<unsigned long long>(c[I]), nxt);
+      if (more) c[I] = acc_combine<F>(c[I], o);
+    });
+    const int nn = __shfl_sync(active, nxt, nxt);
+    const int nm = __shfl_sync(active, more, nxt);
+    if (more) {
+      nxt = nn;
+      more = nm;
+    }
+  }
+  return (peers & ((1u << lane) - 1u)) == 0u;
+}
+
 template <class SH, int GM>
 struct SinkGlobalHash {
   static constexpr int NA = SH::Aggs::N;
@@ -180,10 +215,11 @@ struct SinkGlobalHash {
   __device__ void init() {}
   __device__ __forceinline__ void add(Item<SH>& it, const KParams& kp, int r, bool live) {
     const uint64_t key = pack_key<SH>(it, kp, r);
-    const uint64_t s = global_slot<GM>(g, key, err);
-    if (s > static_cast<uint64_t>(g.cap)) return;
     uint64_t c[NA + 1];
     row_codes<SH>(it, kp, r, live ? ~0ull : 0ull, c);
+    if (g.warp_agg && !warp_preaggregate<SH>(key, c)) return;
+    const uint64_t s = global_slot<GM>(g, key, err);
+    if (s > static_cast<uint64_t>(g.cap)) return;
     slot_atomic_add<SH>(g.vals + s * g.stride, c);
   }
   __device__ void finish() {}
@@ -231,6 +267,7 @@ struct SinkGlobalPerfect {
     }
     uint64_t c[NA + 1];
     row_codes<SH>(it, kp, r, live ? ~0ull : 0ull, c);
+    if (g.warp_agg && !warp_preaggregate<SH>(s, c)) return;
     slot_atomic_add<SH>(g.vals + s * g.stride, c);
   }
   __device__ void finish() {}
@@ -258,6 +295,7 @@ struct SinkLocalPerfect {
     }
     uint64_t c[NA + 1];
     row_codes<SH>(it, kp, r, live ? ~0ull : 0ull, c);
+    if (g.warp_agg && !warp_preaggregate<SH>(s, c)) return;
     slot_atomic_add<SH, true>(sm + s * g.stride, c);
   }
   __device__ void finish() {
@@ -389,6 +427,7 @@ struct SinkLocalHash {
     const uint64_t key = pack_key<SH>(it, kp, r);
     uint64_t c[NA + 1];
     row_codes<SH>(it, kp, r, live ? ~0ull : 0ull, c);
+    if (g.warp_agg && !warp_preaggregate<SH>(key, c)) return;
     if (key != kEmpty64) {
       const uint32_t mask = static_cast<uint32_t>(g.local_slots) - 1;
       uint32_t idx = static_cast<uint32_t>(fmix64(key)) & mask;

@@ -390,6 +390,7 @@ static pv_status resolve_launch(pv_ctx* c, const pv_variant& v, LaunchCfg& L) {
   if (v.access != PV_GRID_STRIDE && v.access != PV_CHUNKED) return fail(c, PV_ERR_INVALID_ARG, "bad access");
   if (v.exec != PV_EXEC_SINGLE_PASS && v.exec != PV_EXEC_MULTI_PASS) return fail(c, PV_ERR_INVALID_ARG, "bad exec");
   if (v.prefetch < 0 || v.prefetch > 16) return fail(c, PV_ERR_INVALID_ARG, "prefetch must be 0..16 trips");
+  if (v.warp_agg != 0 && v.warp_agg != 1) return fail(c, PV_ERR_INVALID_ARG, "warp_agg must be 0 or 1");
   L.pred = v.pred == PV_PREDICATED;
   L.chunk = v.access == PV_CHUNKED;
   L.launches = &c->launches;
@@ -631,6 +632,7 @@ static pv_status alloc_result(pv_ctx* c, Result& r) {
     return fail(c, PV_ERR_INVALID_ARG, "bad aggregation table kind");
   }
   g.max_evictions = 32 * std::max(1, g.log2cap);
+  g.warp_agg = r.var.warp_agg;
   const int64_t slots = g.cap + 1;  // + side slot for the key equal to EMPTY
   g.keys = static_cast<unsigned long long*>(grab(static_cast<size_t>(slots) * 8));
   g.vals = static_cast<unsigned long long*>(grab(static_cast<size_t>(slots) * g.stride * 8));

@@ -107,6 +107,7 @@ struct GroupOut {
   int max_evictions;
   uint64_t seed[4];
   int local_slots;    // LOCAL strategy: slots of the per-CTA shared-memory table
+  int warp_agg;       // atomic sinks: combine a warp's rows of equal key before updating
   // Extraction (dense result columns, int64): out[c * out_cap + row].
   int64_t* out;
   int64_t out_cap;

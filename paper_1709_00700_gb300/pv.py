@@ -81,7 +81,8 @@ class pv_variant(ctypes.Structure):
                 ("access", ctypes.c_int32), ("ht", ctypes.c_int32), ("hash", ctypes.c_int32),
                 ("block", ctypes.c_int32), ("grid_mult", ctypes.c_int32),
                 ("items_per_thread", ctypes.c_int32), ("threads_per_table", ctypes.c_int32),
-                ("cuckoo_k", ctypes.c_int32), ("prefetch", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("cuckoo_k", ctypes.c_int32), ("prefetch", ctypes.c_int32), ("warp_agg", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -163,10 +164,10 @@ class PVError(RuntimeError):
 
 def variant(exec="single", agg="local", pred="branch", access="grid", ht="linear", hash="murmur",
             block=256, grid_mult=0, items_per_thread=2, threads_per_table=0, cuckoo_k=3, seed=0,
-            prefetch=0) -> pv_variant:
+            prefetch=0, warp_agg=0) -> pv_variant:
     """A pv_variant from readable names (the variant dimensions of Section 3.3)."""
     return pv_variant(EXEC[exec], AGG[agg], PRED[pred], ACCESS[access], HT[ht], HASH[hash], block, grid_mult,
-                      items_per_thread, threads_per_table, cuckoo_k, prefetch, seed)
+                      items_per_thread, threads_per_table, cuckoo_k, prefetch, warp_agg, seed)
 
 
 def ht_variant(kind="linear", hash="murmur", cuckoo_k=3, max_evictions=0, load_factor=0.5, seed=0) -> pv_ht_variant:

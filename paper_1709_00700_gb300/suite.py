@@ -45,7 +45,13 @@ GRIDS = {
                      dict(agg="global", ht="perfect"), dict(agg="local", ht="linear"),
                      dict(agg="global", ht="linear"), dict(agg="global", ht="linear", exec="multi"),
                      dict(agg="global", ht="cuckoo", exec="multi"), dict(agg="local", ht="cuckoo", exec="multi")],
-                    ["branch", "predicated"], [0, 1])],
+                    ["branch", "predicated"], [0, 1])] +
+               # warp pre-aggregation before the global tables (hot keys)
+               [dict(s, pred=p, items_per_thread=1, block=256, prefetch=1, warp_agg=1)
+                for s, p in itertools.product(
+                    [dict(agg="global", ht="perfect"), dict(agg="global", ht="linear"),
+                     dict(agg="global", ht="linear", exec="multi"), dict(agg="global", ht="cuckoo", exec="multi")],
+                    ["branch", "predicated"])],
     "star": [dict(s, build=bk, pred=p, items_per_thread=1, block=512, prefetch=f)
              for bk, s, p, f in itertools.product(
                  ["perfect", "linear", "cuckoo"],
@@ -55,7 +61,7 @@ GRIDS = {
 }
 
 
-_DEFAULTS = {"exec": "single", "threads_per_table": 0}
+_DEFAULTS = {"exec": "single", "threads_per_table": 0, "warp_agg": 0}
 
 
 def _normalize(grid: list) -> list:
@@ -187,7 +193,8 @@ class SuiteData:
             self.prepare(q)
             lo, hi = ctx.column_stats("q", "key")
             st.update(sel=max(tot, 0.5) / n, n_preds=1, bytes_in=12, bytes_out=0,
-                      groups=min(hi - lo + 1, q["rows"]), top_share=float(counts.max()) / max(tot, 1))
+                      groups=min(hi - lo + 1, q["rows"]), top_share=float(counts.max()) / max(tot, 1),
+                      collision=_collision(counts))
         else:
             plan = self.prepare(q, n)
             cols = ctx.query(plan, pv.variant(items_per_thread=1, ht="linear"), pv.ht_variant("linear"))
@@ -195,8 +202,16 @@ class SuiteData:
             tot = int(counts.sum())
             st.update(sel=max(tot, 0.5) / n, n_probes=4, bytes_in=24, bytes_out=0,
                       dim_rows=sum(r for _, r, _ in datagen.STAR_DIMS), groups=max(len(counts), 1),
-                      top_share=float(counts.max()) / max(tot, 1) if tot else 0.0)
+                      top_share=float(counts.max()) / max(tot, 1) if tot else 0.0, collision=_collision(counts))
         return st
+
+
+def _collision(counts) -> float:
+    """Probability that two surviving rows drawn at random share a group
+    (sum of squared group shares), from the sample's group counts."""
+    c = np.asarray(counts, dtype=np.float64)
+    t = c.sum()
+    return float(((c / t) ** 2).sum()) if t > 0 else 1.0
 
 
 def time_query(data: SuiteData, q: dict, reps: int = 3) -> dict:
@@ -431,6 +446,7 @@ def main(argv=None):
     ap.add_argument("--out", default="")
     ap.add_argument("--graphs", action="store_true", help="run the CUDA-graph batch experiment only")
     ap.add_argument("--confirm-reps", type=int, default=15, help="re-timing runs per candidate (0 = skip)")
+    ap.add_argument("--restat", action="store_true", help="with --timings-in: recompute the queries' statistics")
     a = ap.parse_args(argv)
     ctx = pv.Context(0)
     if a.graphs:
@@ -443,6 +459,9 @@ def main(argv=None):
             ex = json.load(f)
         ex["stats"] = {int(k): v for k, v in ex["stats"].items()}
         ex["timings"] = {int(k): v for k, v in ex["timings"].items()}
+        if a.restat:
+            data = SuiteData(ctx, a.max_rows)
+            ex["stats"] = {q["id"]: data.stats(q) for q in ex["queries"]}
     else:
         data = SuiteData(ctx, a.max_rows)
         ex = explore(ctx, a.queries, a.max_rows, a.min_rows, reps=a.reps, data=data)

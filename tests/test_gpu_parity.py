@@ -434,3 +434,60 @@ def test_int64_build_keys_are_unsupported(ctx):
     with pytest.raises(pv.PVError) as e:
         ctx.query(plan, pv.variant(), pv.ht_variant("perfect"))
     assert e.value.status == -2
+
+
+# ---------------------------------------------------------------- warp pre-aggregation
+WARP_AGG_VARIANTS = [dict(kw, warp_agg=1) for kw in GROUP_VARIANTS if kw["threads_per_table"] == 0]
+
+
+@pytest.mark.parametrize("g,dist", [(1, "uniform"), (7, "zipf"), (1000, "zipf"), (40_000, "uniform")])
+def test_warp_preaggregation_keyval(ctx, g, dist):
+    kv = {"kv": datagen.table_keyval(90_003, g, dist, seed=100 + g)}
+    register(ctx, kv)
+    for plan, step in ((workloads.keyval_plan(), 3), (workloads.keyval_plan(val_lt=400_000), 5)):
+        w = want(plan, kv)
+        ran = 0
+        for kw in WARP_AGG_VARIANTS[::step]:
+            got = run_or_skip(ctx, plan, pv.variant(**kw))
+            if got is None:
+                continue
+            ran += 1
+            assert_same(got, w, ctxmsg=str(kw))
+        assert ran >= 8
+
+
+def test_warp_preaggregation_lowcard(ctx):
+    li = {"li": datagen.table_lowcard_groups(50_001, seed=12)}
+    register(ctx, li)
+    plan = workloads.lowcard_plan()
+    w = want(plan, li)
+    ran = 0
+    for kw in WARP_AGG_VARIANTS[::2]:
+        got = run_or_skip(ctx, plan, pv.variant(**kw))
+        if got is not None:
+            ran += 1
+            assert_same(got, w, ctxmsg=str(kw))
+    assert ran >= 20
+
+
+def test_warp_preaggregation_min_max_join(ctx):
+    """Table 2's grouped join with SUM, COUNT, MIN and MAX over few groups, so that
+    warps hold many rows of one key (MIN/MAX combine as order-preserving codes)."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "table2_join_group_y.json")))
+    rng = np.random.default_rng(21)
+    n1, n2, n3 = 300, 500, 70_001
+    t1 = {"a": rng.permutation(n1).astype(np.int32), "x": rng.integers(0, 8, n1).astype(np.int32)}
+    t2 = {"b": rng.permutation(n2).astype(np.int32), "y": rng.integers(0, 6, n2).astype(np.int32)}
+    t3 = {"c": rng.integers(0, n1, n3).astype(np.int32), "d": rng.integers(0, n2, n3).astype(np.int32),
+          "z": rng.integers(0, 5, n3).astype(np.int32), "q": rng.integers(-10**12, 10**12, n3).astype(np.int64)}
+    tables = {"T1": t1, "T2": t2, "T3": t3}
+    register(ctx, tables)
+    w = want(g["plan"], tables)
+    assert len(w[0]) >= 3
+    for kind in ("linear", "perfect"):
+        for kw in (dict(), dict(pred="predicated"), dict(agg="global", ht="perfect"), dict(agg="global"),
+                   dict(ht="cuckoo", exec="multi"), dict(agg="local", ht="perfect", pred="predicated")):
+            got = ctx.query(g["plan"], pv.variant(items_per_thread=1, warp_agg=1, **kw), pv.ht_variant(kind))
+            assert_same(got, w, ctxmsg=f"{kind} {kw}")
