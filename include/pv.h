@@ -232,6 +232,11 @@ pv_status pv_result_col_type(pv_ctx* ctx, pv_res res, int32_t col, int32_t* type
  * dst_rows values, on the device if dst_on_device else in host memory. */
 pv_status pv_fetch_result(pv_ctx* ctx, pv_res res, int32_t col, void* dst, int64_t dst_rows,
                           int32_t dst_on_device);
+/* All n_cols result columns at once: column col goes to dst[col], which holds
+ * dst_rows[col] values (device or host memory as for pv_fetch_result).  The
+ * copies are enqueued together and the call synchronises once. */
+pv_status pv_fetch_results(pv_ctx* ctx, pv_res res, int32_t n_cols, void* const* dst, const int64_t* dst_rows,
+                           int32_t dst_on_device);
 /* Releases a table, result or graph handle (columns: forgets the handle). */
 pv_status pv_free(pv_ctx* ctx, int32_t handle);
 

@@ -932,6 +932,41 @@ pv_status pv_fetch_result(pv_ctx* c, pv_res h, int32_t col, void* dst, int64_t d
   return PV_OK;
 }
 
+pv_status pv_fetch_results(pv_ctx* c, pv_res h, int32_t n_cols, void* const* dst, const int64_t* dst_rows,
+                           int32_t on_device) {
+  if (!c || !dst || !dst_rows) return PV_ERR_INVALID_ARG;
+  auto it = c->results.find(h);
+  if (it == c->results.end()) return fail(c, PV_ERR_INVALID_ARG, "unknown result handle");
+  Result& r = *it->second;
+  if (n_cols != r.n_cols) return fail(c, PV_ERR_INVALID_ARG, "n_cols differs from the result's columns");
+  int64_t rows;
+  pv_status s = result_rows(c, r, &rows);
+  if (s != PV_OK) return s;
+  for (int32_t col = 0; col < n_cols; ++col) {
+    if (dst_rows[col] < rows) return fail(c, PV_ERR_INVALID_ARG, "destination too small");
+    if (rows > 0 && !dst[col]) return fail(c, PV_ERR_INVALID_ARG, "null destination");
+  }
+  if (rows == 0) return PV_OK;
+  for (int32_t col = 0; col < n_cols; ++col) {
+    const void* src;
+    size_t bytes;
+    if (r.canon.mode == MODE_AGGREGATE) {
+      src = r.agg.result + col;
+      bytes = 8;
+    } else if (r.canon.mode == MODE_PROJECT) {
+      src = r.proj.col[col];
+      bytes = static_cast<size_t>(rows) * type_size(r.col_type[col]);
+    } else {
+      src = r.grp.out + static_cast<size_t>(col) * r.grp.out_cap;
+      bytes = static_cast<size_t>(rows) * 8;
+    }
+    PV_CUDA(c, cudaMemcpyAsync(dst[col], src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                               c->stream));
+  }
+  PV_CUDA(c, cudaStreamSynchronize(c->stream));
+  return PV_OK;
+}
+
 pv_status pv_free(pv_ctx* c, int32_t h) {
   if (!c) return PV_ERR_INVALID_ARG;
   if (c->capturing) return fail(c, PV_ERR_INVALID_ARG, "cannot free while capturing");

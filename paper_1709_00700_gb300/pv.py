@@ -123,6 +123,8 @@ _SIGS = {
     "pv_mlp_adam": (ctypes.c_int32, [ctypes.c_void_p] + [ctypes.c_void_p] * 4 + [ctypes.c_int64, ctypes.c_float,
                                                                                  ctypes.c_float, ctypes.c_float,
                                                                                  ctypes.c_float, ctypes.c_int32]),
+    "pv_fetch_results": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_void_p),
+                                          _P(ctypes.c_int64), ctypes.c_int32]),
     "pv_atomic_peak": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64,
                                         ctypes.POINTER(ctypes.c_float)]),
     "pv_filter_project_noalloc": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
@@ -365,10 +367,12 @@ class Context:
         for c in range(m.value):
             t = ctypes.c_int32()
             self._check(self.lib.pv_result_col_type(self.h, res, c, ctypes.byref(t)))
-            a = np.empty(max(n.value, 1), dtype=_NP_OF[t.value])
-            self._check(self.lib.pv_fetch_result(self.h, res, c, ctypes.c_void_p(a.ctypes.data), len(a), 0))
-            out.append(a[: n.value])
-        return out
+            out.append(np.empty(max(n.value, 1), dtype=_NP_OF[t.value]))
+        if out:
+            ptrs = (ctypes.c_void_p * len(out))(*[a.ctypes.data for a in out])
+            rows = (ctypes.c_int64 * len(out))(*[len(a) for a in out])
+            self._check(self.lib.pv_fetch_results(self.h, res, len(out), ptrs, rows, 0))
+        return [a[: n.value] for a in out]
 
     def free(self, handle: int):
         self._check(self.lib.pv_free(self.h, handle))
