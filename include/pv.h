@@ -137,7 +137,10 @@ typedef struct {
 /* Variant configuration (Section 3.3, 4, 6; Table 5's dimensions). */
 typedef enum { PV_EXEC_SINGLE_PASS = 0, PV_EXEC_MULTI_PASS = 1 } pv_exec;
 typedef enum { PV_AGG_LOCAL = 0, PV_AGG_GLOBAL = 1 } pv_agg_strategy;
-typedef enum { PV_BRANCH = 0, PV_PREDICATED = 1 } pv_pred_mode;
+/* PV_COMPACTED (grouped pipelines): branched first operation (the filters, else the
+ * first probe); its surviving rows are queued per warp and run one per lane through
+ * the rest of the pipeline, so later operations see full warps. */
+typedef enum { PV_BRANCH = 0, PV_PREDICATED = 1, PV_COMPACTED = 2 } pv_pred_mode;
 typedef enum { PV_GRID_STRIDE = 0, PV_CHUNKED = 1 } pv_access;
 
 typedef struct {

@@ -375,7 +375,7 @@ static pv_status launch_agg(const LaunchCfg& c, const KParams& kp, const AggOut&
       {{launch_agg_t<SH, true, false, 1>, launch_agg_t<SH, true, false, 2>, launch_agg_t<SH, true, false, 4>},
        {launch_agg_t<SH, true, true, 1>, launch_agg_t<SH, true, true, 2>, launch_agg_t<SH, true, true, 4>}}};
   const int ui = c.U == 1 ? 0 : c.U == 2 ? 1 : c.U == 4 ? 2 : -1;
-  if (ui < 0) return PV_ERR_UNSUPPORTED;
+  if (ui < 0 || c.compact) return PV_ERR_UNSUPPORTED;  // compacted mode: grouped pipelines only
   return tab[c.pred][c.chunk][ui](c, kp, out);
 }
 
@@ -388,7 +388,7 @@ static pv_status launch_proj(const LaunchCfg& c, const KParams& kp, const ProjOu
       {{launch_proj_t<SH, true, false, 1>, launch_proj_t<SH, true, false, 2>, launch_proj_t<SH, true, false, 4>},
        {launch_proj_t<SH, true, true, 1>, launch_proj_t<SH, true, true, 2>, launch_proj_t<SH, true, true, 4>}}};
   const int ui = c.U == 1 ? 0 : c.U == 2 ? 1 : c.U == 4 ? 2 : -1;
-  if (ui < 0) return PV_ERR_UNSUPPORTED;
+  if (ui < 0 || c.compact) return PV_ERR_UNSUPPORTED;  // compacted mode: grouped pipelines only
   return tab[c.pred][c.chunk][ui](c, kp, out, exec);
 }
 

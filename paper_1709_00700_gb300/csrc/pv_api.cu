@@ -386,12 +386,14 @@ static pv_status resolve_launch(pv_ctx* c, const pv_variant& v, LaunchCfg& L) {
   if (L.grid_mult < 0) return fail(c, PV_ERR_INVALID_ARG, "grid_mult < 0");
   L.U = v.items_per_thread ? v.items_per_thread : 2;
   if (L.U != 1 && L.U != 2 && L.U != 4) return fail(c, PV_ERR_INVALID_ARG, "items_per_thread must be 1, 2 or 4");
-  if (v.pred != PV_BRANCH && v.pred != PV_PREDICATED) return fail(c, PV_ERR_INVALID_ARG, "bad pred mode");
+  if (v.pred != PV_BRANCH && v.pred != PV_PREDICATED && v.pred != PV_COMPACTED)
+    return fail(c, PV_ERR_INVALID_ARG, "bad pred mode");
   if (v.access != PV_GRID_STRIDE && v.access != PV_CHUNKED) return fail(c, PV_ERR_INVALID_ARG, "bad access");
   if (v.exec != PV_EXEC_SINGLE_PASS && v.exec != PV_EXEC_MULTI_PASS) return fail(c, PV_ERR_INVALID_ARG, "bad exec");
   if (v.prefetch < 0 || v.prefetch > 16) return fail(c, PV_ERR_INVALID_ARG, "prefetch must be 0..16 trips");
   if (v.warp_agg != 0 && v.warp_agg != 1) return fail(c, PV_ERR_INVALID_ARG, "warp_agg must be 0 or 1");
   L.pred = v.pred == PV_PREDICATED;
+  L.compact = v.pred == PV_COMPACTED;
   L.chunk = v.access == PV_CHUNKED;
   L.launches = &c->launches;
   if (c->ktime && !c->capturing) {

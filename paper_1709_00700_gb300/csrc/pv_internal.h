@@ -24,6 +24,7 @@ struct LaunchCfg {
   int grid_mult;  // 0: fill the GPU once (occupancy-derived)
   int U;          // items per thread per trip
   bool pred;      // predicated
+  bool compact;   // compacted: survivors of the first operation queued per warp (grouped pipelines)
   bool chunk;     // chunked access
   int* launches;  // incremented per kernel launch
   // optional per-kernel timing: called right before and right after a launch

@@ -51,13 +51,22 @@ GRIDS = {
                 for s, p in itertools.product(
                     [dict(agg="global", ht="perfect"), dict(agg="global", ht="linear"),
                      dict(agg="global", ht="linear", exec="multi"), dict(agg="global", ht="cuckoo", exec="multi")],
-                    ["branch", "predicated"])],
+                    ["branch", "predicated"])] +
+               # rows passing the filter queued per warp
+               [dict(s, pred="compacted", items_per_thread=1, block=256, prefetch=0)
+                for s in [dict(agg="local", ht="perfect"), dict(agg="global", ht="perfect"),
+                          dict(agg="local", ht="linear"), dict(agg="global", ht="linear")]],
     "star": [dict(s, build=bk, pred=p, items_per_thread=1, block=512, prefetch=f)
              for bk, s, p, f in itertools.product(
                  ["perfect", "linear", "cuckoo"],
                  [dict(agg="local", ht="perfect"), dict(agg="global", ht="perfect"),
                   dict(agg="local", ht="linear"), dict(agg="global", ht="linear")],
-                 ["branch", "predicated"], [0, 1])],
+                 ["branch", "predicated"], [0, 1])] +
+            [dict(s, build=bk, pred="compacted", items_per_thread=1, block=512, prefetch=0)
+             for bk, s in itertools.product(
+                 ["perfect", "linear", "cuckoo"],
+                 [dict(agg="local", ht="perfect"), dict(agg="global", ht="perfect"),
+                  dict(agg="local", ht="linear"), dict(agg="global", ht="linear")])],
 }
 
 

@@ -491,3 +491,80 @@ def test_warp_preaggregation_min_max_join(ctx):
                    dict(ht="cuckoo", exec="multi"), dict(agg="local", ht="perfect", pred="predicated")):
             got = ctx.query(g["plan"], pv.variant(items_per_thread=1, warp_agg=1, **kw), pv.ht_variant(kind))
             assert_same(got, w, ctxmsg=f"{kind} {kw}")
+
+
+# ---------------------------------------------------------------- compacted execution
+COMPACT_VARIANTS = [dict(agg=a, ht=h, pred="compacted", items_per_thread=1, threads_per_table=tp, warp_agg=wa,
+                         block=b, prefetch=pf)
+                    for a, h, tp, wa, b, pf in itertools.product(["local", "global"], ["linear", "cuckoo", "perfect"],
+                                                                 [0, 1], [0, 1], [64, 256, 1024], [0, 1])]
+
+
+def _compacted(ctx, plan, tables, htv=None, step=1, min_ran=10):
+    w = want(plan, tables)
+    ran = 0
+    for kw in COMPACT_VARIANTS[::step]:
+        got = run_or_skip(ctx, plan, pv.variant(**kw), htv)
+        if got is None:
+            continue
+        ran += 1
+        assert_same(got, w, ctxmsg=str(kw))
+    assert ran >= min_ran
+    return ran
+
+
+def test_compacted_filter_first(ctx):
+    li = {"li": datagen.table_lowcard_groups(40_003, seed=13)}
+    register(ctx, li)
+    _compacted(ctx, workloads.lowcard_plan(day_hi=datagen.DAY0 + 300), li, step=3, min_ran=12)
+    for g, dist in ((1000, "zipf"), (50_000, "uniform"), (3, "uniform")):
+        kv = {"kv": datagen.table_keyval(70_001, g, dist, seed=40 + g)}
+        register(ctx, kv)
+        _compacted(ctx, workloads.keyval_plan(val_lt=30_000), kv, step=5, min_ran=8)
+
+
+@pytest.mark.parametrize("build_kind", ["linear", "cuckoo", "perfect"])
+def test_compacted_star_join(ctx, build_kind):
+    s = _star_small(150_007, seed=33)
+    register(ctx, s)
+    for th in ({"d_a": 60, "d_b": 50, "d_c": 30, "d_d": 40}, {"d_a": 20, "d_b": 20, "d_c": 5, "d_d": 10}):
+        _compacted(ctx, workloads.star_plan(th), s, pv.ht_variant(build_kind), step=4, min_ran=8)
+
+
+def test_compacted_min_max_join_and_ragged_tables(ctx):
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "table2_join_group_y.json")))
+    tables = {t: {c: np.array(v["values"], dtype=v["dtype"]) for c, v in cols.items()} for t, cols in g["tables"].items()}
+    register(ctx, tables)
+    for kind in ("linear", "perfect"):
+        for kw in (dict(), dict(agg="global", ht="perfect"), dict(warp_agg=1)):
+            got = ctx.query(g["plan"], pv.variant(items_per_thread=1, pred="compacted", **kw), pv.ht_variant(kind))
+            assert [list(map(int, c)) for c in got] == g["expected"]["cols"]
+    rng = np.random.default_rng(44)
+    for n in (0, 1, 5, 1003):
+        t3 = {"c": rng.integers(0, 4, n).astype(np.int32), "d": rng.integers(0, 5, n).astype(np.int32),
+              "z": rng.integers(0, 5, n).astype(np.int32), "q": rng.integers(-99, 99, n).astype(np.int64)}
+        tabs = {"T1": tables["T1"], "T2": tables["T2"], "T3": t3}
+        register(ctx, {"T3": t3})
+        w = want(g["plan"], tabs)
+        for kw in (dict(), dict(agg="global", ht="perfect")):
+            got = ctx.query(g["plan"], pv.variant(items_per_thread=1, pred="compacted", **kw), pv.ht_variant("perfect"))
+            assert_same(got, w, ctxmsg=f"n={n} {kw}")
+
+
+def test_compacted_is_unsupported_where_it_does_not_apply(ctx):
+    kv = {"kv": datagen.table_keyval(1000, 10, seed=3)}
+    register(ctx, kv)
+    for plan, kw in ((workloads.keyval_plan(), dict()),                             # nothing to compact on
+                     (workloads.keyval_plan(val_lt=5), dict(exec="multi")),         # key pass
+                     (workloads.keyval_plan(val_lt=5), dict(items_per_thread=2)),
+                     (workloads.keyval_plan(val_lt=5), dict(access="chunked"))):
+        with pytest.raises(pv.PVError) as e:
+            ctx.query(plan, pv.variant(pred="compacted", **kw))
+        assert e.value.status == -2
+    t = {"t": datagen.table_filter_agg(1000)}
+    register(ctx, t)
+    with pytest.raises(pv.PVError) as e:
+        ctx.query(workloads.filter_agg_plan(), pv.variant(pred="compacted"))
+    assert e.value.status == -2
