@@ -58,7 +58,7 @@ TUNED = {
     "filter_agg": dict(pred="branch", access="grid", items_per_thread=4, block=512, grid_mult=2),
     "filter_project": dict(exec="single", pred="branch", access="grid", items_per_thread=4, block=128),
     "keyval": dict(agg="local", ht="perfect", pred="branch", access="grid", items_per_thread=1, block=512),
-    "star": dict(agg="global", ht="perfect", pred="branch", access="grid", items_per_thread=1, block=512, prefetch=1),
+    "star": dict(agg="global", ht="perfect", pred="compacted", access="grid", items_per_thread=1, block=512),
 }
 
 

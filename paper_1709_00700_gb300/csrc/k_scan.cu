@@ -112,8 +112,12 @@ __device__ __forceinline__ void write_row(const ProjOut& out, Item<SH>& it, int 
   static_for<PJ::N>([&](auto c) {
     constexpr int C = decltype(c)::value;
     constexpr int S = PJ::slot_of[C];
-    using T = typename At<S, typename SH::Cols::L>::type::T;
-    static_cast<T*>(out.col[C])[pos] = VGet<S>::get(it.v)[r];
+    if constexpr (S >= 0) {
+      using T = typename At<S, typename SH::Cols::L>::type::T;
+      static_cast<T*>(out.col[C])[pos] = VGet<S>::get(it.v)[r];
+    } else {
+      static_cast<int32_t*>(out.col[C])[pos] = it.pay[-S - 1][r];
+    }
   });
 }
 
@@ -430,12 +434,18 @@ using ShKeyValTotals = Shape<Cols<TI64>, Where<P<0>>, Probes<>, Key<>,
 
 // One probe, COUNT(*) of the joining rows (join cardinality).
 using ShJoinCount = Shape<Cols<TI32>, Where<>, Probes<0>, Key<>, Aggs<Count>, Proj<>>;
+// Join then project: the probe's payload beside a fact column, without and
+// with a fact filter in front (Table 2's pipeline shape ending in PROJECT).
+using ShJoinProj = Shape<Cols<TI32, TI64>, Where<>, Probes<0>, Key<>, Aggs<>, Proj<-1, 1>>;
+using ShFilterJoinProj = Shape<Cols<TI32, TI32, TI64>, Where<P<0>>, Probes<1>, Key<>, Aggs<>, Proj<-1, 2>>;
 
 void register_scan_shapes() {
   reg_aggregate<ShJoinCount>();
   reg_aggregate<ShFilterAgg>();
   reg_project<ShFilterProj>();
   reg_project<ShFilterProj1>();
+  reg_project<ShJoinProj>();
+  reg_project<ShFilterJoinProj>();
   reg_aggregate<ShLowcardTotals>();
   reg_aggregate<ShKeyValTotals>();
 }

@@ -350,7 +350,15 @@ static pv_status canonicalize(pv_ctx* c, const pv_pipeline_spec* s, Canon& k) {
   std::string sp = "|P:";
   k.n_proj = s->n_proj;
   for (int i = 0; i < s->n_proj; ++i) {
-    if (s->proj[i].kind != PV_REF_COL) return fail(c, PV_ERR_UNSUPPORTED, "projection of payloads");
+    if (s->proj[i].kind == PV_REF_PAYLOAD) {  // int32 payload of probe a
+      const pv_ref& r = s->proj[i];
+      if (r.a < 0 || r.a >= s->n_probes || r.b != 0 || r.b >= probe_tab[r.a]->n_payload)
+        return fail(c, PV_ERR_INVALID_ARG, "bad payload reference");
+      sp += "p" + std::to_string(r.a) + ",";
+      k.proj_type[i] = PV_I32;
+      continue;
+    }
+    if (s->proj[i].kind != PV_REF_COL) return fail(c, PV_ERR_INVALID_ARG, "bad projection reference");
     int sl = slot(s->proj[i].a);
     if (sl < 0) return bad(sl);
     sp += std::to_string(sl) + ",";

@@ -238,11 +238,16 @@ template <class... Ks> struct Key {
   static void sig(std::string& s) { s += "|K:"; ((Ks::sig(s), s += ","), ...); }
 };
 
+// Projected values in output order: S >= 0 is fact slot S, S < 0 the
+// payload of probe -S - 1 (an int32 output column).
 template <int... S> struct Proj {
   static constexpr int N = sizeof...(S);
   static constexpr int slot_of[N > 0 ? N : 1] = {S...};
-  static constexpr uint32_t slots = (0u | ... | (1u << S));
-  static void sig(std::string& s) { s += "|P:"; ((s += std::to_string(S) + ","), ...); }
+  static constexpr uint32_t slots = (0u | ... | (S >= 0 ? (1u << (S >= 0 ? S : 0)) : 0u));
+  static void sig(std::string& s) {
+    s += "|P:";
+    ((s += (S >= 0 ? std::to_string(S) : "p" + std::to_string(-S - 1)) + ","), ...);
+  }
 };
 
 template <class C, class W, class J, class K, class A, class PJ>

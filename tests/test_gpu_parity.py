@@ -568,3 +568,47 @@ def test_compacted_is_unsupported_where_it_does_not_apply(ctx):
     with pytest.raises(pv.PVError) as e:
         ctx.query(workloads.filter_agg_plan(), pv.variant(pred="compacted"))
     assert e.value.status == -2
+
+
+# ---------------------------------------------------------------- join + project
+PROJ_VARIANTS = [dict(exec=e, pred=p, access=a, items_per_thread=u, block=b)
+                 for e, p, a, u, b in itertools.product(["single", "multi"], ["branch", "predicated"],
+                                                        ["grid", "chunked"], [1, 2, 4], [64, 256])]
+
+
+@pytest.mark.parametrize("n", [0, 7, 4096, 90_003])
+def test_join_project_payloads(ctx, n):
+    """PROJECT of a probe's payload beside a fact column, with and without a
+    fact filter in front: single pass as a multiset, multi pass in input order."""
+    rng = np.random.default_rng(70 + n)
+    D = 5000
+    dim = {"key": rng.permutation(D).astype(np.int32), "f": rng.integers(0, 100, D).astype(np.int32),
+           "g": rng.integers(-1000, 1000, D).astype(np.int32)}
+    fact = {"fk": rng.integers(-10, D + 10, n).astype(np.int32), "z": rng.integers(0, 10, n).astype(np.int32),
+            "rev": rng.integers(-10**12, 10**12, n).astype(np.int64)}
+    register(ctx, {"jpdim": dim, "jpfact": fact})
+    build = [{"table": "jpdim", "key": "key", "filters": [["f", "lt", 30]], "payload": ["g"]}]
+    plans = [{"fact": "jpfact", "builds": build, "probes": [{"build": 0, "fk": "fk"}],
+              "project": [["payload", 0, 0], "rev"]},
+             {"fact": "jpfact", "builds": build, "filters": [["z", "lt", 4]], "probes": [{"build": 0, "fk": "fk"}],
+              "project": [["payload", 0, 0], "rev"]}]
+    tables = {"jpdim": dim, "jpfact": fact}
+    for plan in plans:
+        w = want(plan, tables)
+        for kind in ("perfect", "linear", "cuckoo"):
+            ran = 0
+            for kw in PROJ_VARIANTS[::3]:
+                got = run_or_skip(ctx, plan, pv.variant(**kw), pv.ht_variant(kind))
+                if got is None:
+                    continue
+                ran += 1
+                assert_same(got, w, ordered=kw["exec"] == "multi", ctxmsg=f"{kind} {kw}")
+            assert ran >= 6
+        # result column types: the payload column is int32, the fact column keeps int64
+        hts = ctx.build_all(plan, pv.ht_variant("perfect"))
+        res = ctx.run(plan, pv.variant(), hts)
+        raw = ctx.fetch(res)
+        assert raw[0].dtype == np.int32 and raw[1].dtype == np.int64
+        ctx.free(res)
+        for h in hts:
+            ctx.free(h)
