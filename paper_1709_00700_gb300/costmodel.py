@@ -189,3 +189,52 @@ def pick(net, stats: dict, grid: list) -> tuple:
     pred = net.predict(X)
     i = int(np.argmin(pred))
     return grid[i], pred
+
+
+# ---------------------------------------------------------------------------
+# Run-time re-tuning
+# ---------------------------------------------------------------------------
+class OnlineTuner:
+    """Per-query variant choice that keeps learning from the queries it runs
+    (a run-time optimizer, the paper's future work).
+
+    Every executed query contributes (its features, the measured log time of
+    the variant that ran) to a replay buffer; only the chosen variant's time
+    is observed.  With probability `explore` the network's second choice runs
+    instead of its first, so that the buffer does not only hold the variants
+    the network already likes.  Every `every` observations each network of the
+    ensemble continues training on the whole buffer for `steps` Adam steps
+    (its weights, moments and step count carry over; the standardisation
+    fitted on the seed data stays)."""
+
+    def __init__(self, model: Ensemble, X: np.ndarray, y: np.ndarray, every: int = 16, steps: int = 400,
+                 lr: float = 5e-4, explore: float = 0.1, cap: int = 50_000, seed: int = 0):
+        self.model = model
+        self.X = [np.asarray(x, np.float64) for x in X]
+        self.y = [float(v) for v in y]
+        self.every, self.steps, self.lr, self.explore, self.cap = every, steps, lr, explore, cap
+        self.rng = np.random.default_rng(seed)
+        self.pending = 0
+        self.updates = 0
+
+    def choose(self, stats: dict, grid: list) -> dict:
+        X = np.stack([features(stats, v) for v in grid])
+        order = np.argsort(self.model.predict(X))
+        if len(order) > 1 and self.rng.random() < self.explore:
+            return grid[int(order[1])]
+        return grid[int(order[0])]
+
+    def observe(self, stats: dict, variant: dict, ms: float):
+        if not (ms > 0 and math.isfinite(ms)):
+            return
+        self.X.append(features(stats, variant))
+        self.y.append(math.log(ms))
+        if len(self.X) > self.cap:
+            del self.X[0], self.y[0]
+        self.pending += 1
+        if self.pending >= self.every:
+            X, y = np.stack(self.X), np.asarray(self.y)
+            for net in self.model.nets:
+                net.train(X, y, epochs=self.steps, lr=self.lr, report_every=self.steps)
+            self.pending = 0
+            self.updates += 1

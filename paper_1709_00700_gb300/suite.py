@@ -434,6 +434,44 @@ def confirm(data: SuiteData, ex: dict, summary: dict, reps: int = 15, top: int =
             "per_query": rows}
 
 
+def online_experiment(ctx: "pv.Context", ex: dict, n_seed: int = 100, tail: int = 100, seed_epochs: int = 10000,
+                      ensemble: int = 3, lr: float = 2e-3, every: int = 16, steps: int = 400,
+                      explore: float = 0.1) -> dict:
+    """Run-time re-tuning: a network trained on the first n_seed queries (all
+    their variants timed) then meets the other queries one at a time, in a
+    seeded random order.  For each it picks a variant, observes only that
+    variant's time (from the exhaustive timings) and learns from it
+    (costmodel.OnlineTuner).  Over the last `tail` queries of the stream, the
+    online picks are judged against the exhaustive best beside the picks of
+    the seed network left as it was."""
+    queries, stats, timings = ex["queries"], ex["stats"], ex["timings"]
+    rng = np.random.default_rng(ex.get("seed", 1709) + 7)
+    order = [queries[i] for i in rng.permutation(len(queries))]
+    seed_qs, stream = order[:n_seed], order[n_seed:]
+    X, y = _rows(seed_qs, stats, timings)
+    static, _ = _fit(ctx, X, y, seed_epochs, ensemble, lr, 1709)
+    online, _ = _fit(ctx, X, y, seed_epochs, ensemble, lr, 1709)
+    tuner = costmodel.OnlineTuner(online, X, y, every=every, steps=steps, explore=explore)
+    t0 = time.time()
+    r_static, r_online = [], []
+    for q in stream:
+        tm = timings[q["id"]]
+        finite = [v for v in GRIDS[grid_key(q)] if math.isfinite(tm[autotune.variant_key(v)])]
+        best = min(tm[autotune.variant_key(v)] for v in finite)
+        v = tuner.choose(stats[q["id"]], finite)
+        ms = tm[autotune.variant_key(v)]
+        tuner.observe(stats[q["id"]], v, ms)
+        r_online.append(ms / best)
+        p, _ = costmodel.pick(static, stats[q["id"]], finite)
+        r_static.append(tm[autotune.variant_key(p)] / best)
+    ro, rs = np.array(r_online[-tail:]), np.array(r_static[-tail:])
+    gm = lambda r: float(np.exp(np.mean(np.log(r))))  # noqa: E731
+    return {"seed_queries": n_seed, "stream": len(stream), "tail": len(ro), "updates": tuner.updates,
+            "explore": explore, "seconds": time.time() - t0,
+            "online_within_10pct": float(np.mean(ro <= 1.10)), "online_geomean": gm(ro),
+            "static_within_10pct": float(np.mean(rs <= 1.10)), "static_geomean": gm(rs)}
+
+
 def run(ctx: "pv.Context", n_queries: int = 500, max_rows: int = 300_000_000, min_rows: int = 1_000_000,
         n_train: int | None = None, seed: int = 1709, reps: int = 3, candidates=CANDIDATES, log=print) -> dict:
     ex = explore(ctx, n_queries, max_rows, min_rows, seed, reps, log)
@@ -456,6 +494,7 @@ def main(argv=None):
     ap.add_argument("--graphs", action="store_true", help="run the CUDA-graph batch experiment only")
     ap.add_argument("--confirm-reps", type=int, default=15, help="re-timing runs per candidate (0 = skip)")
     ap.add_argument("--restat", action="store_true", help="with --timings-in: recompute the queries' statistics")
+    ap.add_argument("--online", action="store_true", help="also run the run-time re-tuning experiment")
     a = ap.parse_args(argv)
     ctx = pv.Context(0)
     if a.graphs:
@@ -482,6 +521,8 @@ def main(argv=None):
     if a.confirm_reps > 0:
         data = data or SuiteData(ctx, a.max_rows)
         summary["confirmed"] = confirm(data, ex, summary, reps=a.confirm_reps)
+    if a.online:
+        summary["online"] = online_experiment(ctx, ex)
     print(json.dumps({k: (v if k != "confirmed" else {kk: vv for kk, vv in v.items() if kk != "per_query"})
                       for k, v in summary.items() if k != "per_query"}))
     if a.out:

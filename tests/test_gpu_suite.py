@@ -37,3 +37,13 @@ def test_confirm_retimes_the_held_out_candidates():
     for r in c["per_query"]:
         assert r["pick_ratio"] >= 1.0 and r["config_ratio"] >= 1.0 and math.isfinite(r["pick_ratio"])
     assert 0.0 <= c["mlp_within_10pct"] <= 1.0
+
+
+def test_online_tuner_learns_from_its_own_runs():
+    ctx = pv.Context(0)
+    data = suite.SuiteData(ctx, 2_000_000)
+    ex = suite.explore(ctx, 30, 2_000_000, 200_000, reps=2, log=None, data=data)
+    r = suite.online_experiment(ctx, ex, n_seed=10, tail=10, seed_epochs=200, ensemble=1, every=4, steps=50)
+    ctx.close()
+    assert r["stream"] == 20 and r["updates"] == 5
+    assert 0.0 <= r["online_within_10pct"] <= 1.0 and r["online_geomean"] >= 1.0 and r["static_geomean"] >= 1.0
