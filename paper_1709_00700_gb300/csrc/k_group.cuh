@@ -25,6 +25,7 @@ namespace pv {
 
 constexpr int kLocalProbe = 16;          // probe-length bound in a local table
 constexpr size_t kLocalBytes = 96 << 10; // shared memory of a CTA-local table
+constexpr size_t kClusterBytes = 192 << 10;  // shared memory of one CTA's part of a cluster table
 
 __device__ __forceinline__ uint64_t perfect_index(const GroupDesc& gd, int64_t p0, int64_t p1, bool& ok) {
   const int64_t a = p0 - gd.key_min[0];
@@ -311,6 +312,123 @@ struct SinkLocalPerfect {
   }
 };
 
+// Perfect array partitioned over the CTAs of a thread-block cluster
+// (distributed shared memory): slot s lives in CTA s mod kClusterCTAs of the
+// cluster, at local slot s / kClusterCTAs, so a cluster keeps kClusterCTAs
+// times the domain one CTA could on chip, and neighbouring (often equally
+// hot) slots spread over its CTAs.  Rows update the owner's words with
+// cluster-scope shared-memory atomics: sums as two 32-bit fetch-adds (the
+// high word only on a carry or a non-zero high part, as shared_add64), MIN /
+// MAX codes with a 64-bit compare-and-swap loop.  Prologue: zero the local part, cluster
+// barrier (no update reaches unzeroed memory).  Epilogue: cluster barrier
+// (every update has landed), then each CTA merges its part into the global
+// table with one atomic per non-zero word.  Every thread of every CTA of the
+// cluster reaches both barriers.
+constexpr int kClusterCTAs = 8;
+
+// Cluster-wide barrier (not .aligned: the threads of a warp may reach it
+// diverged, e.g. after a grid-stride loop).
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// Address of the same shared-memory offset in cluster CTA `rank`.
+__device__ __forceinline__ uint32_t cluster_map(uint32_t local, uint32_t rank) {
+  uint32_t remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(rank));
+  return remote;
+}
+__device__ __forceinline__ void cluster_add64(uint32_t addr, uint64_t x) {
+  const uint32_t lo = static_cast<uint32_t>(x);
+  uint32_t hi = static_cast<uint32_t>(x >> 32);
+  if (lo) {
+    uint32_t old;
+    asm volatile("atom.shared::cluster.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(addr), "r"(lo) : "memory");
+    hi += (old + lo < old) ? 1u : 0u;
+  }
+  if (hi) {
+    uint32_t old;
+    asm volatile("atom.shared::cluster.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(addr + 4), "r"(hi) : "memory");
+  }
+}
+// 64-bit max into a cluster CTA's shared memory by compare-and-swap: a probe
+// of atom.shared::cluster.max.u64 on this part lost updates (339 of 512
+// words wrong after 131k updates), while 64-bit CAS and the 32-bit atomics
+// were exact.  Every failed CAS sees a strictly larger value, so the loop
+// ends; the cap only guards it.  Returns false when the cap was reached.
+__device__ __forceinline__ bool cluster_max64(uint32_t addr, uint64_t x) {
+  unsigned long long cur;
+  asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(cur) : "r"(addr) : "memory");
+  for (int it = 0; it < (1 << 20) && cur < x; ++it) {
+    unsigned long long old;
+    asm volatile("atom.shared::cluster.cas.b64 %0, [%1], %2, %3;"
+                 : "=l"(old)
+                 : "r"(addr), "l"(cur), "l"(static_cast<unsigned long long>(x))
+                 : "memory");
+    if (old == cur) return true;
+    cur = old;
+  }
+  return cur >= x;
+}
+
+template <class SH>
+struct SinkClusterPerfect {
+  static constexpr int NA = SH::Aggs::N;
+  static constexpr bool kCluster = true;
+  static __host__ __device__ int64_t part_slots(int64_t cap) { return (cap + kClusterCTAs - 1) / kClusterCTAs; }
+  const GroupDesc& gd; const GroupOut& g; int32_t* err; unsigned long long* sm;
+  uint32_t sbase, rank;
+  __device__ SinkClusterPerfect(const GroupDesc& d, const GroupOut& o, int32_t* e, unsigned long long* s)
+      : gd(d), g(o), err(e), sm(s), sbase(static_cast<uint32_t>(__cvta_generic_to_shared(s))), rank(cluster_rank()) {}
+  __device__ void init() {
+    const int64_t words = part_slots(g.cap) * g.stride;
+    for (int64_t i = threadIdx.x; i < words; i += blockDim.x) sm[i] = 0;
+    cluster_sync();
+  }
+  __device__ __forceinline__ void add(Item<SH>& it, const KParams& kp, int r, bool live) {
+    bool ok;
+    uint64_t s = row_perfect_index<SH>(gd, it, kp, r, ok);
+    if (!ok) {
+      if (live) { set_error(err, PV_ERR_KEY_OUT_OF_RANGE); return; }
+      s = 0;
+    }
+    uint64_t c[NA + 1];
+    row_codes<SH>(it, kp, r, live ? ~0ull : 0ull, c);
+    if (g.warp_agg && !warp_preaggregate<SH>(s, c)) return;
+    const uint32_t base = cluster_map(
+        sbase + static_cast<uint32_t>(s / kClusterCTAs) * static_cast<uint32_t>(g.stride) * 8u,
+        static_cast<uint32_t>(s % kClusterCTAs));
+    using A = typename SH::Aggs;
+    static_for<NA + 1>([&](auto a) {
+      constexpr int I = decltype(a)::value;
+      constexpr int F = I < NA ? A::func_of[I < NA ? I : 0] : PV_COUNT;
+      if constexpr (I == NA && count_index<A>() >= 0) return;
+      if (c[I]) {
+        if constexpr (F == PV_SUM || F == PV_COUNT) cluster_add64(base + I * 8, c[I]);
+        else if (!cluster_max64(base + I * 8, c[I])) set_error(err, PV_ERR_TIMEOUT);
+      }
+    });
+  }
+  __device__ void finish() {
+    cluster_sync();
+    const int64_t words = part_slots(g.cap) * g.stride;
+    for (int64_t i = threadIdx.x; i < words; i += blockDim.x) {
+      const uint64_t v = sm[i];
+      if (!v) continue;
+      const int64_t slot = (i / g.stride) * kClusterCTAs + rank;
+      const int a = static_cast<int>(i % g.stride);
+      if (slot >= g.cap) continue;
+      unsigned long long* dst = g.vals + slot * g.stride + a;
+      if (a == NA || gd.func[a] == PV_SUM || gd.func[a] == PV_COUNT) atomicAdd(dst, static_cast<unsigned long long>(v));
+      else atomicMax(dst, static_cast<unsigned long long>(v));
+    }
+  }
+};
+
 // Thread-private perfect arrays (M = 1): no atomics until the CTA epilogue.
 // A slot holds SW words (the aggregates, the row count unless a COUNT
 // aggregate already counts rows, padded to an even count) stored as SW / 2
@@ -532,6 +650,10 @@ __device__ __forceinline__ void extract_slots(const GroupDesc& gd, const GroupOu
 // pipelined predicated loop unless the sink states otherwise.
 template <class S, class = void> struct SinkRegs { static constexpr int value = 128; };
 template <class S> struct SinkRegs<S, std::void_t<decltype(S::kRegs)>> { static constexpr int value = S::kRegs; };
+template <class S, class = void> struct SinkIsCluster { static constexpr bool value = false; };
+template <class S> struct SinkIsCluster<S, std::void_t<decltype(S::kCluster)>> {
+  static constexpr bool value = S::kCluster;
+};
 template <class S, class = void> struct SinkPipelined { static constexpr bool value = true; };
 template <class S> struct SinkPipelined<S, std::void_t<decltype(S::kPipelined)>> {
   static constexpr bool value = S::kPipelined;
@@ -796,24 +918,70 @@ static pv_status run_group_compact(const LaunchCfg& c, const KParams& kp, const 
   }
 }
 
+// Launch as clusters of kClusterCTAs CTAs: the grid is the co-resident
+// clusters times kClusterCTAs (or grid_mult x SMs rounded down to whole
+// clusters), unsupported when no cluster of this kernel fits.
+template <class K>
+static pv_status launch_k_cluster(const LaunchCfg& c, K k, const KParams& kp, const GroupDesc& gd,
+                                  const GroupOut& g, size_t smem) {
+  if (smem > 48 * 1024) {
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
+      return PV_ERR_UNSUPPORTED;
+  }
+  cudaLaunchConfig_t cfg{};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kClusterCTAs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(c.block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = c.stream;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3(kClusterCTAs);
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, k, &cfg) != cudaSuccess || clusters <= 0) {
+    cudaGetLastError();
+    return PV_ERR_UNSUPPORTED;
+  }
+  int64_t grid = c.grid_mult > 0 ? (static_cast<int64_t>(c.grid_mult) * c.sm_count) / kClusterCTAs * kClusterCTAs
+                                 : static_cast<int64_t>(clusters) * kClusterCTAs;
+  grid = std::max<int64_t>(kClusterCTAs, std::min<int64_t>(grid, static_cast<int64_t>(clusters) * kClusterCTAs));
+  cfg.gridDim = dim3(static_cast<unsigned>(grid));
+  kmark(c);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k, kp, gd, g);
+  kmark(c);
+  ++*c.launches;
+  return e == cudaSuccess ? PV_OK : PV_ERR_CUDA;
+}
+
 // UMASK: bit 0 = unroll 1 compiled, bit 1 = unroll 2 compiled.
 template <class SH, int UMASK, template <class> class SinkT>
 static pv_status run_group(const LaunchCfg& c, const KParams& kp, const GroupDesc& gd, const GroupOut& g, size_t smem) {
   using S = SinkT<SH>;
-  if (c.compact) return run_group_compact<SH, SinkT>(c, kp, gd, g, smem);
-  if constexpr ((UMASK & 1) != 0) if (c.U == 1) {
-    if (c.pred) return c.chunk ? launch_k(c, k_group<SH, true, true, 1, S>, kp, gd, g, smem, 1)
-                               : launch_k(c, k_group<SH, true, false, 1, S>, kp, gd, g, smem, 1);
-    return c.chunk ? launch_k(c, k_group<SH, false, true, 1, S>, kp, gd, g, smem, 1)
-                   : launch_k(c, k_group<SH, false, false, 1, S>, kp, gd, g, smem, 1);
+  if constexpr (SinkIsCluster<S>::value) {
+    if (c.compact || c.U != 1) return PV_ERR_UNSUPPORTED;
+    if (c.pred) return c.chunk ? launch_k_cluster(c, k_group<SH, true, true, 1, S>, kp, gd, g, smem)
+                               : launch_k_cluster(c, k_group<SH, true, false, 1, S>, kp, gd, g, smem);
+    return c.chunk ? launch_k_cluster(c, k_group<SH, false, true, 1, S>, kp, gd, g, smem)
+                   : launch_k_cluster(c, k_group<SH, false, false, 1, S>, kp, gd, g, smem);
+  } else {
+    if (c.compact) return run_group_compact<SH, SinkT>(c, kp, gd, g, smem);
+    if constexpr ((UMASK & 1) != 0) if (c.U == 1) {
+      if (c.pred) return c.chunk ? launch_k(c, k_group<SH, true, true, 1, S>, kp, gd, g, smem, 1)
+                                 : launch_k(c, k_group<SH, true, false, 1, S>, kp, gd, g, smem, 1);
+      return c.chunk ? launch_k(c, k_group<SH, false, true, 1, S>, kp, gd, g, smem, 1)
+                     : launch_k(c, k_group<SH, false, false, 1, S>, kp, gd, g, smem, 1);
+    }
+    if constexpr ((UMASK & 2) != 0) if (c.U == 2) {
+      if (c.pred) return c.chunk ? launch_k(c, k_group<SH, true, true, 2, S>, kp, gd, g, smem, 2)
+                                 : launch_k(c, k_group<SH, true, false, 2, S>, kp, gd, g, smem, 2);
+      return c.chunk ? launch_k(c, k_group<SH, false, true, 2, S>, kp, gd, g, smem, 2)
+                     : launch_k(c, k_group<SH, false, false, 2, S>, kp, gd, g, smem, 2);
+    }
+    return PV_ERR_UNSUPPORTED;
   }
-  if constexpr ((UMASK & 2) != 0) if (c.U == 2) {
-    if (c.pred) return c.chunk ? launch_k(c, k_group<SH, true, true, 2, S>, kp, gd, g, smem, 2)
-                               : launch_k(c, k_group<SH, true, false, 2, S>, kp, gd, g, smem, 2);
-    return c.chunk ? launch_k(c, k_group<SH, false, true, 2, S>, kp, gd, g, smem, 2)
-                   : launch_k(c, k_group<SH, false, false, 2, S>, kp, gd, g, smem, 2);
-  }
-  return PV_ERR_UNSUPPORTED;
 }
 
 template <class SH, int UMASK, int HTK>
@@ -843,7 +1011,15 @@ static pv_status launch_group(const LaunchCfg& c, const KParams& kp, const Group
   const bool multi = v.exec == PV_EXEC_MULTI_PASS;
   const bool local = v.agg == PV_AGG_LOCAL;
   if (multi && c.compact) return PV_ERR_UNSUPPORTED;  // the key pass has no compacted form
-  if (v.agg != PV_AGG_LOCAL && v.agg != PV_AGG_GLOBAL) return PV_ERR_INVALID_ARG;
+  if (v.agg != PV_AGG_LOCAL && v.agg != PV_AGG_GLOBAL && v.agg != PV_AGG_CLUSTER) return PV_ERR_INVALID_ARG;
+  if (v.agg == PV_AGG_CLUSTER) {  // perfect arrays in the distributed shared memory of a cluster
+    if (g.ht != PV_HT_PERFECT || multi || v.threads_per_table == 1) return PV_ERR_UNSUPPORTED;
+    const size_t smem = static_cast<size_t>(SinkClusterPerfect<SH>::part_slots(g.cap)) * g.stride * 8;
+    if (smem > kClusterBytes) return PV_ERR_UNSUPPORTED;
+    const pv_status s = run_group<SH, UMASK, SinkClusterPerfect>(c, kp, gd, g, smem);
+    if (s != PV_OK) return s;
+    return launch_dedupe_extract(c, gd, g, false);
+  }
   const size_t slot_bytes = static_cast<size_t>(g.stride) * 8;
   pv_status s;
   if (g.ht == PV_HT_PERFECT) {

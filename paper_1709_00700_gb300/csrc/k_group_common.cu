@@ -45,6 +45,7 @@ void register_group_keyval();
 void register_group_keyval_f();
 void register_group_star();
 void register_group_join2();
+void register_group_join2y();
 
 void register_group_shapes() {
   register_group_lowcard();
@@ -52,6 +53,7 @@ void register_group_shapes() {
   register_group_keyval_f();
   register_group_star();
   register_group_join2();
+  register_group_join2y();
 }
 
 }  // namespace pv

@@ -31,7 +31,7 @@ REF_COL, REF_PAYLOAD = 0, 1
 HT = {"linear": 0, "cuckoo": 1, "perfect": 2}
 HASH = {"murmur": 0, "multshift": 1}
 EXEC = {"single": 0, "multi": 1}
-AGG = {"local": 0, "global": 1}
+AGG = {"local": 0, "global": 1, "cluster": 2}
 PRED = {"branch": 0, "predicated": 1, "compacted": 2}
 ACCESS = {"grid": 0, "chunked": 1}
 _NP_OF = {PV_I32: np.int32, PV_I64: np.int64, PV_U8: np.uint8}

@@ -612,3 +612,68 @@ def test_join_project_payloads(ctx, n):
         ctx.free(res)
         for h in hts:
             ctx.free(h)
+
+
+# ---------------------------------------------------------------- cluster (distributed shared memory) tables
+CLUSTER_VARIANTS = [dict(agg="cluster", ht="perfect", pred=p, access=a, items_per_thread=1, block=b, warp_agg=wa,
+                         grid_mult=gm)
+                    for p, a, b, wa, gm in itertools.product(["branch", "predicated"], ["grid", "chunked"],
+                                                             [128, 512], [0, 1], [0, 1])]
+
+
+def _cluster(ctx, plan, tables, htv=None, step=1, min_ran=8):
+    w = want(plan, tables)
+    ran = 0
+    for kw in CLUSTER_VARIANTS[::step]:
+        got = run_or_skip(ctx, plan, pv.variant(**kw), htv)
+        if got is None:
+            continue
+        ran += 1
+        assert_same(got, w, ctxmsg=str(kw))
+    assert ran >= min_ran
+
+
+@pytest.mark.parametrize("g,dist", [(1, "uniform"), (1000, "zipf"), (30_000, "uniform"), (60_000, "zipf")])
+def test_cluster_tables_keyval(ctx, g, dist):
+    kv = {"kv": datagen.table_keyval(150_007, g, dist, seed=200 + g)}
+    register(ctx, kv)
+    _cluster(ctx, workloads.keyval_plan(), kv, step=2)
+    _cluster(ctx, workloads.keyval_plan(val_lt=200_000), kv, step=5, min_ran=4)
+
+
+def test_cluster_tables_lowcard_star_and_min_max(ctx):
+    li = {"li": datagen.table_lowcard_groups(30_001, seed=14)}
+    register(ctx, li)
+    _cluster(ctx, workloads.lowcard_plan(), li, step=3, min_ran=5)
+    s = _star_small(80_001, seed=35)
+    register(ctx, s)
+    _cluster(ctx, workloads.star_plan({"d_a": 60, "d_b": 50, "d_c": 30, "d_d": 40}), s, pv.ht_variant("perfect"),
+             step=3, min_ran=5)
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "table2_join_group_y.json")))
+    rng = np.random.default_rng(23)
+    n1, n2, n3 = 300, 500, 40_001
+    tables = {"T1": {"a": rng.permutation(n1).astype(np.int32), "x": rng.integers(0, 8, n1).astype(np.int32)},
+              "T2": {"b": rng.permutation(n2).astype(np.int32), "y": rng.integers(0, 600, n2).astype(np.int32)},
+              "T3": {"c": rng.integers(0, n1, n3).astype(np.int32), "d": rng.integers(0, n2, n3).astype(np.int32),
+                     "z": rng.integers(0, 5, n3).astype(np.int32),
+                     "q": rng.integers(-10**12, 10**12, n3).astype(np.int64)}}
+    register(ctx, tables)
+    _cluster(ctx, g["plan"], tables, pv.ht_variant("perfect"), step=4, min_ran=3)
+
+
+def test_cluster_tables_unsupported_cases(ctx):
+    kv = {"kv": datagen.table_keyval(10_000, 100, seed=9)}
+    register(ctx, kv)
+    plan = workloads.keyval_plan()
+    for kw in (dict(ht="linear"), dict(ht="cuckoo", exec="multi"), dict(exec="multi"), dict(threads_per_table=1),
+               dict(pred="compacted"), dict(items_per_thread=2)):
+        with pytest.raises(pv.PVError) as e:
+            ctx.query(plan, pv.variant(**dict(dict(agg="cluster", ht="perfect", items_per_thread=1), **kw)))
+        assert e.value.status == -2, kw
+    big = {"kv": {"key": np.array([0, 10_000_000], np.int32), "val": np.array([1, 2], np.int64)}}
+    register(ctx, big)  # a 1e7-slot domain does not fit the shared memory of a cluster
+    with pytest.raises(pv.PVError) as e:
+        ctx.query(plan, pv.variant(agg="cluster", ht="perfect", items_per_thread=1))
+    assert e.value.status == -2
