@@ -355,10 +355,10 @@ __device__ __forceinline__ void cluster_add64(uint32_t addr, uint64_t x) {
     asm volatile("atom.shared::cluster.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(addr + 4), "r"(hi) : "memory");
   }
 }
-// 64-bit max into a cluster CTA's shared memory by compare-and-swap: a probe
-// of atom.shared::cluster.max.u64 on this part lost updates (339 of 512
-// words wrong after 131k updates), while 64-bit CAS and the 32-bit atomics
-// were exact.  Every failed CAS sees a strictly larger value, so the loop
+// 64-bit max into a cluster CTA's shared memory by compare-and-swap: on
+// sm_103a, atom.shared::cluster.max.u64 lost updates in a probe (339 of 512
+// words wrong after 131k updates from one cluster), while 64-bit CAS and the
+// 32-bit cluster atomics were exact.  Every failed CAS sees a strictly larger value, so the loop
 // ends; the cap only guards it.  Returns false when the cap was reached.
 __device__ __forceinline__ bool cluster_max64(uint32_t addr, uint64_t x) {
   unsigned long long cur;
