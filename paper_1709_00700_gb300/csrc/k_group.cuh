@@ -711,145 +711,22 @@ __global__ void __maxnreg__((GroupRegs<SH, Sink, PRED>::value)) k_group(const __
   sink.finish();
 }
 
-// ---------------------------------------------------------------------------
-// Compacted execution (variant pred = PV_COMPACTED).  The pipeline's first
-// operation (its filters, or else its first probe) runs over whole items as
-// in branched mode; the rows it keeps are appended to a queue per warp in
-// shared memory, and each 32 queued rows are taken one per lane through the
-// remaining operations (the probes, the loads of the sink's columns) and
-// the sink.  After a selective first operation the later operations then
-// run on full warps, not on the few live lanes of every warp.  Queue
-// entries are 32-bit row indices (tables of fewer than 2^32 rows).
-// ---------------------------------------------------------------------------
-constexpr int kQueueCap = 32 + 128;  // a drain leaves < 32 rows; one trip appends at most 32 lanes x 4 rows
-
-// Whether an expression tree (Key, Aggs, Proj and their terms) reads the
-// payload bound by probe J.
-template <int J, class T> struct RefPay : std::false_type {};
-template <int J, int I> struct RefPay<J, PL<J, I>> : std::true_type {};
-template <int J, template <class...> class Tm, class... Ts>
-struct RefPay<J, Tm<Ts...>> : std::bool_constant<(RefPay<J, Ts>::value || ...)> {};
-
-// The row stage repeats the first probe only to bind its payload: when the
-// first operation was that probe and nothing reads its payload, it is skipped.
-template <class SH>
-constexpr bool compact_skip_probe0() {
-  return SH::Where::N == 0 && !RefPay<0, typename SH::Key>::value && !RefPay<0, typename SH::Aggs>::value &&
-         !RefPay<0, typename SH::Proj>::value;
-}
-
-// Columns the sink reads for a queued row beyond the probe keys the row stage
-// loads (a skipped first probe's key column counts as not loaded).
-template <class SH>
-constexpr uint32_t compact_row_slots() {
-  constexpr uint32_t probed = compact_skip_probe0<SH>() ? SH::Probes::slots & ~(1u << SH::Probes::slot_of[0])
-                                                        : SH::Probes::slots;
-  return (SH::Key::slots | SH::Aggs::slots | SH::Proj::slots) & ~probed;
-}
-
-// First operation of an item (nvalid = 0 past the table): its filters, or
-// else its first probe; leaves the surviving rows in it.mask.
-template <class SH>
-__device__ __forceinline__ void compact_first(Item<SH>& it, const KParams& kp, int64_t item) {
-  using W = typename SH::Where;
-  using JP = typename SH::Probes;
-  const int64_t left = kp.n_rows - item * 4;
-  it.nvalid = left >= 4 ? 4 : (left > 0 ? static_cast<int>(left) : 0);
-  it.mask = (1u << it.nvalid) - 1u;
-  if constexpr (W::N > 0) {
-    load_slots<SH, W::slots>(it, kp, item);
-    static_for<W::N>([&](auto j) { it.mask &= pred_bits<SH, decltype(j)::value>(it, kp); });
-  } else {
-    constexpr int S = JP::slot_of[0];
-    load_slots<SH, (1u << S)>(it, kp, item);
-    it.mask = probe_item(kp.probe[0], VGet<S>::get(it.v), it.mask, it.pay[0], false);
-  }
-}
-
-// One queued row through the probes (the first probe again when it was the
-// first operation: that binds its payload), the column loads and the sink.
-template <class SH, class Sink>
-__device__ __forceinline__ void compact_row(Sink& sink, const KParams& kp, uint32_t row) {
-  using JP = typename SH::Probes;
-  Item<SH> it;
-  it.nvalid = 1;
-  it.mask = 1u;
-  bool ok = true;
-  static_for<JP::N>([&](auto j) {
-    constexpr int J = decltype(j)::value;
-    constexpr int S = JP::slot_of[J];
-    using T = typename At<S, typename SH::Cols::L>::type::T;
-    if (J == 0 && compact_skip_probe0<SH>()) {
-      it.pay[J][0] = 0;  // the first operation was this probe, and its payload is not read
-    } else if (ok) {
-      const T key = __ldg(static_cast<const T*>(kp.col[S]) + row);
-      VGet<S>::get(it.v)[0] = key;
-      int32_t p = 0;
-      ok = probe_key(kp.probe[J], static_cast<int64_t>(key), p);
-      it.pay[J][0] = p;
-    }
-  });
-  if (!ok) return;
-  static_for<SH::Cols::N>([&](auto c) {
-    constexpr int S = decltype(c)::value;
-    if constexpr ((compact_row_slots<SH>() >> S) & 1u) {
-      using T = typename At<S, typename SH::Cols::L>::type::T;
-      VGet<S>::get(it.v)[0] = __ldg(static_cast<const T*>(kp.col[S]) + row);
-    }
-  });
-  sink.add(it, kp, 0, true);
-}
-
+// Compacted execution of a grouped pipeline: for_rows_compacted queues the
+// survivors of the first operation per warp; each queued row runs the other
+// probes, the sink's column loads and the sink, one row per lane.
 template <class SH, class Sink>
 __global__ void __maxnreg__((GroupRegs<SH, Sink, false>::value)) k_group_compact(
     const __grid_constant__ KParams kp, const __grid_constant__ GroupDesc gd, const __grid_constant__ GroupOut g) {
   extern __shared__ unsigned long long smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  uint32_t* q = reinterpret_cast<uint32_t*>(smem) + warp * kQueueCap;
+  const int nwarps = blockDim.x >> 5;
+  uint32_t* q = reinterpret_cast<uint32_t*>(smem) + (threadIdx.x >> 5) * kQueueCap;
   if (blockIdx.x == 0 && threadIdx.x == 0) *g.out_count = 0;  // extraction runs after this kernel
   Sink sink(gd, g, kp.err, smem + nwarps * kQueueCap / 2);     // 640 bytes of queue per warp
   sink.init();
-  const uint32_t lt = (1u << lane) - 1u;
-  int qlen = 0;  // warp-uniform
-  auto drain = [&](int n) {
-    if (lane < n) compact_row<SH>(sink, kp, q[lane]);
-    __syncwarp();
-    uint32_t keep[(kQueueCap - 32 + 31) / 32];
-#pragma unroll
-    for (int i = 0; i < (kQueueCap - 32 + 31) / 32; ++i) {
-      const int k = n + lane + 32 * i;
-      keep[i] = k < qlen ? q[k] : 0u;
-    }
-    __syncwarp();
-#pragma unroll
-    for (int i = 0; i < (kQueueCap - 32 + 31) / 32; ++i) {
-      const int k = lane + 32 * i;
-      if (k < qlen - n) q[k] = keep[i];
-    }
-    __syncwarp();
-    qlen -= n;
-  };
-  const int64_t T = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int64_t n_full = kp.n_rows >> 2;
-  const int pf = kp.prefetch;
-  const LanePrefetch<SH, first_stage_slots<SH>()> lp(kp, lane);
-  for (int d = 1; d < pf; ++d) lp.issue((t - lane) + d * T, n_full);
-  for (int64_t wb = t - lane; wb < kp.n_items; wb += T) {  // every lane of a warp runs every trip
-    if (pf > 0) lp.issue(wb + pf * T, n_full);
+  for_rows_compacted<SH>(kp, q, [&](uint32_t row) {
     Item<SH> it;
-    compact_first(it, kp, wb + lane);
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const bool live = (it.mask >> r) & 1u;
-      const uint32_t b = __ballot_sync(0xffffffffu, live);
-      if (live) q[qlen + __popc(b & lt)] = static_cast<uint32_t>((wb + lane) * 4 + r);
-      qlen += __popc(b);
-    }
-    __syncwarp();
-    while (qlen >= 32) drain(32);
-  }
-  if (qlen > 0) drain(qlen);
+    if (compact_load_row<SH>(it, kp, row)) sink.add(it, kp, 0, true);
+  });
   pdl_launch_dependents();
   sink.finish();
 }

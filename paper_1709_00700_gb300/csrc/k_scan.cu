@@ -17,6 +17,56 @@ namespace pv {
 // reduction, one shared-memory pass per CTA, one atomic per CTA and
 // aggregate; the last CTA decodes the result and re-zeroes the accumulators.
 // ---------------------------------------------------------------------------
+// CTA epilogue of the ungrouped aggregation: warp shuffles, one slot per warp
+// in shared memory, one atomic per aggregate per CTA; the last CTA to finish
+// decodes the MIN/MAX codes into the result and resets the accumulators.
+template <class SH>
+__device__ __forceinline__ void aggregate_epilogue(uint64_t (&acc)[SH::Aggs::N + 1], const AggOut& out) {
+  using A = typename SH::Aggs;
+  constexpr int NA = A::N;
+  __shared__ unsigned long long red[32][NA + 1];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  static_for<NA + 1>([&](auto a) {
+    constexpr int I = decltype(a)::value;
+    constexpr int F = I < NA ? A::func_of[I < NA ? I : 0] : PV_COUNT;
+    acc[I] = warp_reduce<F>(acc[I]);
+  });
+  if (lane == 0) {
+#pragma unroll
+    for (int a = 0; a <= NA; ++a) red[warp][a] = acc[a];
+  }
+  __syncthreads();
+  if (warp == 0) {
+    static_for<NA + 1>([&](auto a) {
+      constexpr int I = decltype(a)::value;
+      constexpr int F = I < NA ? A::func_of[I < NA ? I : 0] : PV_COUNT;
+      uint64_t v = lane < nwarps ? red[lane][I] : 0;
+      v = warp_reduce<F>(v);
+      if (lane == 0 && v != 0) acc_atomic<F>(out.acc + I, v);
+    });
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(out.done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    const uint64_t rows = atomicExch(out.acc + NA, 0ull);
+    static_for<NA>([&](auto a) {
+      constexpr int I = decltype(a)::value;
+      constexpr int F = A::func_of[I];
+      const uint64_t c = atomicExch(out.acc + I, 0ull);
+      int64_t v = static_cast<int64_t>(c);
+      if constexpr (F == PV_MIN) v = rows ? decode_min(c) : 0;
+      if constexpr (F == PV_MAX) v = rows ? decode_max(c) : 0;
+      out.result[I] = v;
+    });
+    *out.done = 0;
+  }
+}
+
 template <class SH, bool PRED, bool CHUNK, int U>
 __global__ void __maxnreg__(128) k_aggregate(const __grid_constant__ KParams kp, const __grid_constant__ AggOut out) {
   using A = typename SH::Aggs;
@@ -60,47 +110,7 @@ __global__ void __maxnreg__(128) k_aggregate(const __grid_constant__ KParams kp,
     });
   }
 
-  __shared__ unsigned long long red[32][NA + 1];
-  __shared__ bool last;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  static_for<NA + 1>([&](auto a) {
-    constexpr int I = decltype(a)::value;
-    constexpr int F = I < NA ? A::func_of[I < NA ? I : 0] : PV_COUNT;
-    acc[I] = warp_reduce<F>(acc[I]);
-  });
-  if (lane == 0) {
-#pragma unroll
-    for (int a = 0; a <= NA; ++a) red[warp][a] = acc[a];
-  }
-  __syncthreads();
-  if (warp == 0) {
-    static_for<NA + 1>([&](auto a) {
-      constexpr int I = decltype(a)::value;
-      constexpr int F = I < NA ? A::func_of[I < NA ? I : 0] : PV_COUNT;
-      uint64_t v = lane < nwarps ? red[lane][I] : 0;
-      v = warp_reduce<F>(v);
-      if (lane == 0 && v != 0) acc_atomic<F>(out.acc + I, v);
-    });
-  }
-  if (threadIdx.x == 0) {
-    __threadfence();
-    last = atomicAdd(out.done, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
-    const uint64_t rows = atomicExch(out.acc + NA, 0ull);
-    static_for<NA>([&](auto a) {
-      constexpr int I = decltype(a)::value;
-      constexpr int F = A::func_of[I];
-      const uint64_t c = atomicExch(out.acc + I, 0ull);
-      int64_t v = static_cast<int64_t>(c);
-      if constexpr (F == PV_MIN) v = rows ? decode_min(c) : 0;
-      if constexpr (F == PV_MAX) v = rows ? decode_max(c) : 0;
-      out.result[I] = v;
-    });
-    *out.done = 0;
-  }
+  aggregate_epilogue<SH>(acc, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -326,6 +336,48 @@ __global__ void __maxnreg__(128) k_project_scatter(const __grid_constant__ KPara
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
+// Compacted execution of an ungrouped aggregation: the rows that survive the
+// first operation are queued per warp and accumulated one per lane.
+template <class SH>
+__global__ void __maxnreg__(128) k_aggregate_compact(const __grid_constant__ KParams kp,
+                                                     const __grid_constant__ AggOut out) {
+  using A = typename SH::Aggs;
+  constexpr int NA = A::N;
+  extern __shared__ uint32_t qmem[];
+  uint64_t acc[NA + 1];
+#pragma unroll
+  for (int a = 0; a <= NA; ++a) acc[a] = 0;
+  for_rows_compacted<SH>(kp, qmem + (threadIdx.x >> 5) * kQueueCap, [&](uint32_t row) {
+    Item<SH> it;
+    if (!compact_load_row<SH>(it, kp, row)) return;
+    static_for<NA>([&](auto a) {
+      constexpr int I = decltype(a)::value;
+      using AG = typename At<I, typename A::L>::type;
+      acc[I] = acc_combine<AG::func>(acc[I], acc_code<AG::func>(agg_value<AG>(it, kp, 0)));
+    });
+    acc[NA] += 1;
+  });
+  aggregate_epilogue<SH>(acc, out);
+}
+
+template <class SH>
+static pv_status launch_agg_compact(const LaunchCfg& c, const KParams& kp, const AggOut& out) {
+  if constexpr (SH::Where::N == 0 && SH::Probes::N == 0) {
+    return PV_ERR_UNSUPPORTED;  // nothing to compact on
+  } else {
+    if (c.chunk || c.U != 1 || kp.n_rows > static_cast<int64_t>(UINT32_MAX)) return PV_ERR_UNSUPPORTED;
+    auto k = k_aggregate_compact<SH>;
+    const size_t smem = static_cast<size_t>(c.block / 32) * kQueueCap * 4;
+    const int grid = grid_for(c, reinterpret_cast<const void*>(k), smem, kp.n_items, c.block);
+    if (grid <= 0) return PV_ERR_UNSUPPORTED;
+    kmark(c);
+    k<<<grid, c.block, smem, c.stream>>>(kp, out);
+    kmark(c);
+    ++*c.launches;
+    return cudaGetLastError() == cudaSuccess ? PV_OK : PV_ERR_CUDA;
+  }
+}
+
 template <class SH, bool P, bool C, int U>
 static pv_status launch_agg_t(const LaunchCfg& c, const KParams& kp, const AggOut& out) {
   auto k = k_aggregate<SH, P, C, U>;
@@ -378,8 +430,9 @@ static pv_status launch_agg(const LaunchCfg& c, const KParams& kp, const AggOut&
        {launch_agg_t<SH, false, true, 1>, launch_agg_t<SH, false, true, 2>, launch_agg_t<SH, false, true, 4>}},
       {{launch_agg_t<SH, true, false, 1>, launch_agg_t<SH, true, false, 2>, launch_agg_t<SH, true, false, 4>},
        {launch_agg_t<SH, true, true, 1>, launch_agg_t<SH, true, true, 2>, launch_agg_t<SH, true, true, 4>}}};
+  if (c.compact) return launch_agg_compact<SH>(c, kp, out);
   const int ui = c.U == 1 ? 0 : c.U == 2 ? 1 : c.U == 4 ? 2 : -1;
-  if (ui < 0 || c.compact) return PV_ERR_UNSUPPORTED;  // compacted mode: grouped pipelines only
+  if (ui < 0) return PV_ERR_UNSUPPORTED;
   return tab[c.pred][c.chunk][ui](c, kp, out);
 }
 
@@ -392,7 +445,7 @@ static pv_status launch_proj(const LaunchCfg& c, const KParams& kp, const ProjOu
       {{launch_proj_t<SH, true, false, 1>, launch_proj_t<SH, true, false, 2>, launch_proj_t<SH, true, false, 4>},
        {launch_proj_t<SH, true, true, 1>, launch_proj_t<SH, true, true, 2>, launch_proj_t<SH, true, true, 4>}}};
   const int ui = c.U == 1 ? 0 : c.U == 2 ? 1 : c.U == 4 ? 2 : -1;
-  if (ui < 0 || c.compact) return PV_ERR_UNSUPPORTED;  // compacted mode: grouped pipelines only
+  if (ui < 0 || c.compact) return PV_ERR_UNSUPPORTED;  // compacted mode: aggregations only
   return tab[c.pred][c.chunk][ui](c, kp, out, exec);
 }
 

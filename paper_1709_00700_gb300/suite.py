@@ -35,7 +35,9 @@ SAMPLE_ROWS = 65_536
 GRIDS = {
     "filter_aggregate": [dict(pred=p, access=a, items_per_thread=u, block=b, prefetch=f)
                          for p, a, u, b, f in itertools.product(["branch", "predicated"], ["grid", "chunked"],
-                                                                [1, 4], [256, 512], [0, 1])],
+                                                                [1, 4], [256, 512], [0, 1])] +
+                        [dict(pred="compacted", access="grid", items_per_thread=1, block=b, prefetch=f)
+                         for b, f in itertools.product([256, 512], [0, 1])],
     "filter_project": [dict(exec=e, pred=p, access=a, items_per_thread=u, block=256, prefetch=f)
                        for e, p, a, u, f in itertools.product(["single", "multi"], ["branch", "predicated"],
                                                               ["grid", "chunked"], [1, 4], [0, 1])],

@@ -565,9 +565,48 @@ def test_compacted_is_unsupported_where_it_does_not_apply(ctx):
         assert e.value.status == -2
     t = {"t": datagen.table_filter_agg(1000)}
     register(ctx, t)
-    with pytest.raises(pv.PVError) as e:
-        ctx.query(workloads.filter_agg_plan(), pv.variant(pred="compacted"))
+    with pytest.raises(pv.PVError) as e:  # projections have no compacted form
+        ctx.query(workloads.filter_project_plan(), pv.variant(pred="compacted", items_per_thread=1))
     assert e.value.status == -2
+
+
+@pytest.mark.parametrize("n", [0, 1, 5, 4097, 200_003])
+def test_compacted_ungrouped_aggregates(ctx, n):
+    t = {"t": datagen.table_filter_agg(n, seed=n + 3)}
+    register(ctx, t)
+    for plan in (workloads.filter_agg_plan(), workloads.filter_agg_plan(a_lt=100, b_lo=0, b_hi=99),
+                 workloads.filter_agg_plan(a_lt=0)):
+        w = want(plan, t)
+        for kw in (dict(block=64), dict(block=256, prefetch=1), dict(block=1024, grid_mult=1)):
+            got = ctx.query(plan, pv.variant(pred="compacted", items_per_thread=1, **kw))
+            assert_same(got, w, ctxmsg=f"{plan['filters']} {kw}")
+    kv = {"kv": datagen.table_keyval(n, 50, seed=n + 4)}
+    register(ctx, kv)
+    plan = {"fact": "kv", "filters": [["val", "lt", 300_000]],
+            "aggs": [["sum", [["x", "val"]]], ["count"], ["min", [["x", "val"]]], ["max", [["x", "val"]]]]}
+    w = want(plan, kv)
+    got = ctx.query(plan, pv.variant(pred="compacted", items_per_thread=1))
+    if n:
+        assert_same(got, w, ctxmsg="keyval totals")
+    else:
+        assert int(got[1][0]) == 0 and int(got[0][0]) == 0
+    li = {"li": datagen.table_lowcard_groups(n, seed=n + 5)}
+    register(ctx, li)
+    plan = dict(workloads.lowcard_plan(), group_by=[])
+    w = want(plan, li)
+    assert_same(ctx.query(plan, pv.variant(pred="compacted", items_per_thread=1)), w, ctxmsg="lowcard totals")
+
+
+def test_compacted_join_count(ctx):
+    D, r, thr = 1234, 3, 37
+    dim = {"key": np.arange(D, dtype=np.int32), "f": (np.arange(D) % 100).astype(np.int32)}
+    fact = {"fk": (np.arange(D * r) % D).astype(np.int32)}
+    register(ctx, {"cjdim": dim, "cjfact": fact})
+    plan = {"fact": "cjfact", "builds": [{"table": "cjdim", "key": "key", "filters": [["f", "lt", thr]], "payload": []}],
+            "probes": [{"build": 0, "fk": "fk"}], "aggs": [["count"]]}
+    for kind in ("linear", "cuckoo", "perfect"):
+        got = ctx.query(plan, pv.variant(pred="compacted", items_per_thread=1), pv.ht_variant(kind))
+        assert int(got[0][0]) == r * ((D // 100) * thr + min(D % 100, thr))
 
 
 # ---------------------------------------------------------------- join + project
