@@ -30,7 +30,8 @@ FAMILIES = ("filter", "grouped", "star")
 PLAN_FEATURES = ("log_rows", "sel", "log_sel", "log_groups", "log_groups_per_row", "top_share", "n_preds",
                  "n_probes", "log_dim_rows", "bytes_in", "bytes_out", "n_aggs", "project", "log_bytes",
                  "log_out_rows", "fam_filter", "fam_grouped", "fam_star", "log_hot_rows", "log_groups_hit",
-                 "log_rows_per_group", "log_collision", "warp_repeats")
+                 "log_rows_per_group", "log_collision", "warp_repeats", "sel_first", "log_sel_first",
+                 "log_sel_after_first")
 VARIANT_FEATURES = ("multi", "local", "ht_linear", "ht_cuckoo", "ht_perfect", "multshift", "predicated",
                     "chunked", "log_block", "grid_mult", "unroll", "private_tables", "prefetch", "build_linear",
                     "build_cuckoo", "build_perfect", "warp_agg", "compacted", "cluster")
@@ -48,6 +49,7 @@ def plan_vector(st: dict) -> list:
     fam = st["family"]
     # without a measured collision probability: uniform over the groups, or one group when filtering
     coll = float(st["collision"]) if "collision" in st else (1.0 if fam == "filter" else 1.0 / groups)
+    sel1 = min(1.0, max(float(st.get("sel_first", sel)), sel))
     return [math.log10(rows), sel, math.log10(sel), math.log10(groups), math.log10(groups / rows),
             float(st.get("top_share", 0.0)), float(st.get("n_preds", 0)), float(st.get("n_probes", 0)),
             math.log10(1.0 + float(st.get("dim_rows", 0))), float(st.get("bytes_in", 0)),
@@ -60,7 +62,9 @@ def plan_vector(st: dict) -> list:
             math.log10(max(1.0, rows * sel / max(1.0, min(groups, rows * sel)))),
             # key repeats: probability that two surviving rows share a group, and the expected
             # number of other rows of a 32-row warp step holding the same key
-            math.log10(max(coll, 1e-9)), min(31.0, 31.0 * coll)]
+            math.log10(max(coll, 1e-9)), min(31.0, 31.0 * coll),
+            # the first operation's own selectivity (what compacted execution queues) and the rest's
+            sel1, math.log10(sel1), math.log10(min(1.0, sel / sel1))]
 
 
 def variant_vector(v: dict) -> list:

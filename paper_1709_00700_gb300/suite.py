@@ -214,6 +214,12 @@ class SuiteData:
             cols = ctx.query(plan, pv.variant(items_per_thread=1, ht="linear"), pv.ht_variant("linear"))
             counts = cols[3]
             tot = int(counts.sum())
+            # rows surviving the first probe alone (what compacted execution queues)
+            b0 = plan["builds"][plan["probes"][0]["build"]]
+            first = {"fact": plan["fact"], "builds": [b0], "probes": [{"build": 0, "fk": plan["probes"][0]["fk"]}],
+                     "aggs": [["count"]]}
+            c1 = int(ctx.query(first, pv.variant(items_per_thread=1), pv.ht_variant("perfect"))[0][0])
+            st["sel_first"] = max(c1, 0.5) / n
             st.update(sel=max(tot, 0.5) / n, n_probes=4, bytes_in=24, bytes_out=0,
                       dim_rows=sum(r for _, r, _ in datagen.STAR_DIMS), groups=max(len(counts), 1),
                       top_share=float(counts.max()) / max(tot, 1) if tot else 0.0, collision=_collision(counts))
