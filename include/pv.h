@@ -160,10 +160,10 @@ typedef struct {
   int32_t cuckoo_k;          /* aggregation cuckoo hash functions (0 = 3) */
   int32_t prefetch;          /* grid-stride pipelines: bulk-prefetch each warp's column chunks this
                                 many loop trips ahead into L2 (0 = off) */
-  int32_t warp_agg;          /* HASH_AGGREGATE with atomic tables (local or global, not thread-private):
-                                1 = lanes of a warp holding the same group key first combine their
-                                aggregates (match_any), one lane updates the table (Section 4's local
-                                pre-aggregation applied within a warp); 0 = every row updates */
+  int32_t warp_agg;          /* HASH_AGGREGATE into global or cluster tables: 1 = lanes of a warp holding
+                                the same group key first combine their aggregates (match_any), one lane
+                                updates the table (Section 4's local pre-aggregation applied within a
+                                warp); 0 = every row updates.  Shared-memory (local) tables ignore it. */
   uint64_t seed;             /* aggregation hash seeds */
 } pv_variant;
 

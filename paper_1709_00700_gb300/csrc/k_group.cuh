@@ -173,9 +173,11 @@ __device__ __forceinline__ uint64_t global_slot(const GroupOut& g, uint64_t key,
   else return global_lookup<PV_HT_CUCKOO>(g, key, err);
 }
 
-// Warp pre-aggregation of the atomic sinks (variant flag warp_agg): the
-// active lanes holding the same group key combine their accumulator codes,
-// and the group's lowest lane alone updates the table.  The lanes of a group
+// Warp pre-aggregation in front of the global and cluster tables (variant
+// flag warp_agg; shared-memory tables ignore it: their atomics cost less
+// than the matching): the active lanes holding the same group key combine
+// their accumulator codes, and the group's lowest lane alone updates the
+// table.  The lanes of a group
 // form a list in lane order; pointer jumping (each step adds the successor's
 // partial and skips to the successor's successor) leaves the whole group's
 // combination in its first lane after ceil(log2(group size)) steps.  One
@@ -269,7 +271,7 @@ struct SinkGlobalPerfect {
     uint64_t c[NA + 1];
     row_codes<SH>(it, kp, r, live ? ~0ull : 0ull, c);
     if (g.warp_agg && !warp_preaggregate<SH>(s, c)) return;
-    slot_atomic_add<SH>(g.vals + s * g.stride, c);
+    slot_atomic_add<SH>(g.vals + (blockIdx.x % g.replicas) * g.rep_stride + s * g.stride, c);
   }
   __device__ void finish() {}
 };
@@ -296,8 +298,7 @@ struct SinkLocalPerfect {
     }
     uint64_t c[NA + 1];
     row_codes<SH>(it, kp, r, live ? ~0ull : 0ull, c);
-    if (g.warp_agg && !warp_preaggregate<SH>(s, c)) return;
-    slot_atomic_add<SH, true>(sm + s * g.stride, c);
+    slot_atomic_add<SH, true>(sm + s * g.stride, c);  // (warp_agg applies to global and cluster tables)
   }
   __device__ void finish() {
     __syncthreads();
@@ -306,8 +307,9 @@ struct SinkLocalPerfect {
       const uint64_t v = sm[i];
       if (!v) continue;
       const int a = static_cast<int>(i % g.stride);
-      if (a == NA || gd.func[a] == PV_SUM || gd.func[a] == PV_COUNT) atomicAdd(g.vals + i, static_cast<unsigned long long>(v));
-      else atomicMax(g.vals + i, static_cast<unsigned long long>(v));
+      unsigned long long* dst = g.vals + (blockIdx.x % g.replicas) * g.rep_stride + i;
+      if (a == NA || gd.func[a] == PV_SUM || gd.func[a] == PV_COUNT) atomicAdd(dst, static_cast<unsigned long long>(v));
+      else atomicMax(dst, static_cast<unsigned long long>(v));
     }
   }
 };
@@ -422,7 +424,7 @@ struct SinkClusterPerfect {
       const int64_t slot = (i / g.stride) * kClusterCTAs + rank;
       const int a = static_cast<int>(i % g.stride);
       if (slot >= g.cap) continue;
-      unsigned long long* dst = g.vals + slot * g.stride + a;
+      unsigned long long* dst = g.vals + (blockIdx.x % g.replicas) * g.rep_stride + slot * g.stride + a;
       if (a == NA || gd.func[a] == PV_SUM || gd.func[a] == PV_COUNT) atomicAdd(dst, static_cast<unsigned long long>(v));
       else atomicMax(dst, static_cast<unsigned long long>(v));
     }
@@ -519,7 +521,7 @@ struct SinkThreadPerfect {
       }
       v = add ? warp_reduce<PV_SUM>(v) : warp_reduce<PV_MAX>(v);
       if (lane == 0 && v) {
-        unsigned long long* dst = g.vals + slot * g.stride;
+        unsigned long long* dst = g.vals + (blockIdx.x % g.replicas) * g.rep_stride + slot * g.stride;
         if (a == NA) atomicAdd(dst + NA, static_cast<unsigned long long>(v));  // row count word
         else if (add) atomicAdd(dst + a, static_cast<unsigned long long>(v));
         else atomicMax(dst + a, static_cast<unsigned long long>(v));
@@ -545,7 +547,6 @@ struct SinkLocalHash {
     const uint64_t key = pack_key<SH>(it, kp, r);
     uint64_t c[NA + 1];
     row_codes<SH>(it, kp, r, live ? ~0ull : 0ull, c);
-    if (g.warp_agg && !warp_preaggregate<SH>(key, c)) return;
     if (key != kEmpty64) {
       const uint32_t mask = static_cast<uint32_t>(g.local_slots) - 1;
       uint32_t idx = static_cast<uint32_t>(fmix64(key)) & mask;
@@ -639,6 +640,43 @@ __device__ __forceinline__ void extract_slots(const GroupDesc& gd, const GroupOu
       for (int a = 0; a <= na; ++a) v[a] = 0;
       if (!perfect && s < g.cap) g.keys[s] = kEmpty64;
     }
+  }
+}
+
+// Extraction of a replicated perfect table: one warp per slot (warp w of W
+// takes slots w, w + W, ...).  Lane r reads replica r's words (independent
+// loads, one round trip), a warp reduction folds them (add, or max of the
+// MIN/MAX codes), lane 0 appends the group and each lane empties its replica.
+__device__ __forceinline__ void extract_replicated(const GroupDesc& gd, const GroupOut& g, int64_t t, int64_t T) {
+  const int lane = threadIdx.x & 31;
+  const int na = gd.n_aggs;
+  const bool mine = lane < g.replicas;
+  for (int64_t s = t >> 5; s < g.cap; s += T >> 5) {
+    unsigned long long* v = g.vals + s * g.stride + (mine ? lane : 0) * g.rep_stride;
+    uint64_t w[PV_MAX_AGGS + 1];
+#pragma unroll
+    for (int a = 0; a <= PV_MAX_AGGS; ++a) w[a] = (a <= na && mine) ? __ldcg(v + a) : 0;
+#pragma unroll
+    for (int a = 0; a <= PV_MAX_AGGS; ++a) {
+      if (a > na) break;
+      const bool add = a == na || gd.func[a] == PV_SUM || gd.func[a] == PV_COUNT;
+      w[a] = add ? warp_reduce<PV_SUM>(w[a]) : warp_reduce<PV_MAX>(w[a]);
+    }
+    if (w[gd.count_word] == 0) continue;  // the same for every lane after the reduction
+    if (lane == 0) {
+      const int64_t pos = static_cast<int64_t>(atomicAdd(g.out_count, 1ull));
+      if (pos < g.out_cap) {
+        if (gd.n_keys == 1) {
+          g.out[pos] = gd.key_min[0] + s;
+        } else {
+          g.out[pos] = gd.key_min[0] + s / gd.key_span[1];
+          g.out[g.out_cap + pos] = gd.key_min[1] + s % gd.key_span[1];
+        }
+        for (int a = 0; a < na; ++a) g.out[(gd.n_keys + a) * g.out_cap + pos] = decode_agg(gd.func[a], w[a]);
+      }
+    }
+    if (mine)
+      for (int a = 0; a <= na; ++a) v[a] = 0;
   }
 }
 

@@ -22,13 +22,16 @@ __global__ void k_cuckoo_dedupe(const __grid_constant__ GroupOut g) {
 
 __global__ void k_extract(const __grid_constant__ GroupDesc gd, const __grid_constant__ GroupOut g) {
   pdl_wait();  // launched early behind the aggregation kernel
-  extract_slots(gd, g, static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x,
-                static_cast<int64_t>(gridDim.x) * blockDim.x);
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t T = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  if (g.replicas > 1) extract_replicated(gd, g, t, T);
+  else extract_slots(gd, g, t, T);
 }
 
 pv_status launch_dedupe_extract(const LaunchCfg& c, const GroupDesc& gd, const GroupOut& g, bool dedupe) {
   const int64_t total = g.cap + 1;
-  const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(c.sm_count * 8, (total + 255) / 256)));
+  const int64_t threads = g.replicas > 1 ? total * 32 : total;  // replicated: one warp per slot
+  const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(c.sm_count * 8, (threads + 255) / 256)));
   kmark(c);
   cudaError_t e = cudaSuccess;
   if (dedupe) k_cuckoo_dedupe<<<grid, 256, 0, c.stream>>>(g);

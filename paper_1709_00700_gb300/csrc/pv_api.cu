@@ -644,8 +644,11 @@ static pv_status alloc_result(pv_ctx* c, Result& r) {
   g.max_evictions = 32 * std::max(1, g.log2cap);
   g.warp_agg = r.var.warp_agg;
   const int64_t slots = g.cap + 1;  // + side slot for the key equal to EMPTY
+  g.replicas = g.ht == PV_HT_PERFECT && g.cap <= kReplicatedSlots ? kReplicas : 1;
+  g.rep_stride = slots * g.stride;
+  const size_t val_bytes = static_cast<size_t>(slots) * g.stride * 8 * g.replicas;
   g.keys = static_cast<unsigned long long*>(grab(static_cast<size_t>(slots) * 8));
-  g.vals = static_cast<unsigned long long*>(grab(static_cast<size_t>(slots) * g.stride * 8));
+  g.vals = static_cast<unsigned long long*>(grab(val_bytes));
   const int ncol = k.n_keys + k.n_aggs;
   g.out_cap = std::min<int64_t>(slots, std::max<int64_t>(k.n_rows, 1));
   g.out = static_cast<int64_t*>(grab(static_cast<size_t>(g.out_cap) * ncol * 8));
@@ -653,7 +656,7 @@ static pv_status alloc_result(pv_ctx* c, Result& r) {
   if (!g.keys || !g.vals || !g.out || !g.out_count) return fail(c, PV_ERR_OOM, "allocator returned NULL");
   // Empty table once at allocation; extraction empties every slot it reads.
   PV_CUDA(c, cudaMemsetAsync(g.keys, 0xFF, static_cast<size_t>(slots) * 8, c->stream));
-  PV_CUDA(c, cudaMemsetAsync(g.vals, 0, static_cast<size_t>(slots) * g.stride * 8, c->stream));
+  PV_CUDA(c, cudaMemsetAsync(g.vals, 0, val_bytes, c->stream));
   PV_CUDA(c, cudaMemsetAsync(g.out_count, 0, 16, c->stream));
   r.n_cols = ncol;
   for (int i = 0; i < ncol; ++i) r.col_type[i] = PV_I64;

@@ -93,6 +93,10 @@ struct GroupDesc {
   int64_t key_span[PV_MAX_KEYS];
 };
 
+// Perfect tables of at most kReplicatedSlots slots get kReplicas copies.
+constexpr int64_t kReplicatedSlots = 64;
+constexpr int kReplicas = 16;
+
 // Grouped aggregation table + extraction buffers (owned by a result).
 struct GroupOut {
   // Global table.  Slot s: keys[s] (EMPTY = ~0; perfect: unused) and
@@ -109,6 +113,11 @@ struct GroupOut {
   uint64_t seed[4];
   int local_slots;    // LOCAL strategy: slots of the per-CTA shared-memory table
   int warp_agg;       // atomic sinks: combine a warp's rows of equal key before updating
+  // Perfect tables of few slots are replicated: CTA b adds into replica
+  // b % replicas (vals + replica * rep_stride), which spreads the atomics of
+  // many CTAs on the same few words; extraction folds the replicas.
+  int replicas;       // 1 for hashed tables
+  int64_t rep_stride; // words between replicas: (cap + 1) * stride
   // Extraction (dense result columns, int64): out[c * out_cap + row].
   int64_t* out;
   int64_t out_cap;
