@@ -6,7 +6,7 @@ run-time, per-query optimizer as future work (Section 9.4).  Here a small
 network predicts the log run time of (query, variant) pairs from plan
 features, column statistics and variant features; the pick for a query is
 the variant with the smallest prediction.  Exhaustive search stays the
-fallback and the judge.
+fallback and the yardstick.
 
 Every forward pass, gradient and Adam step runs in libpv's kernels
 (pv_mlp_forward / pv_mlp_backward / pv_mlp_adam); this module holds the

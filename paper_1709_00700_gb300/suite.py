@@ -342,7 +342,7 @@ def _evaluate(model, qs, stats, timings, configs=None, top_k=3):
     return out
 
 
-def judge(ctx: "pv.Context", ex: dict, n_train: int | None = None, candidates=CANDIDATES, top_k: int = 3,
+def assess(ctx: "pv.Context", ex: dict, n_train: int | None = None, candidates=CANDIDATES, top_k: int = 3,
           n_val: int | None = None) -> dict:
     """Trains the cost model on the training queries' timings and judges its
     picks on the held-out queries against the exhaustive best, beside the
@@ -486,7 +486,7 @@ def online_experiment(ctx: "pv.Context", ex: dict, n_seed: int = 100, tail: int 
 def run(ctx: "pv.Context", n_queries: int = 500, max_rows: int = 300_000_000, min_rows: int = 1_000_000,
         n_train: int | None = None, seed: int = 1709, reps: int = 3, candidates=CANDIDATES, log=print) -> dict:
     ex = explore(ctx, n_queries, max_rows, min_rows, seed, reps, log)
-    return judge(ctx, ex, n_train, candidates)
+    return assess(ctx, ex, n_train, candidates)
 
 
 def main(argv=None):
@@ -499,7 +499,7 @@ def main(argv=None):
     ap.add_argument("--epochs", type=int, default=0, help="fixed training setting instead of validation choice")
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--ensemble", type=int, default=5)
-    ap.add_argument("--timings-in", default="", help="judge saved exploration results instead of timing again")
+    ap.add_argument("--timings-in", default="", help="assess saved exploration results instead of timing again")
     ap.add_argument("--timings-out", default="")
     ap.add_argument("--out", default="")
     ap.add_argument("--graphs", action="store_true", help="run the CUDA-graph batch experiment only")
@@ -528,7 +528,7 @@ def main(argv=None):
             with open(a.timings_out, "w") as f:
                 json.dump(ex, f)
     cands = ((a.epochs, a.ensemble, a.lr),) if a.epochs else CANDIDATES
-    summary = judge(ctx, ex, candidates=cands)
+    summary = assess(ctx, ex, candidates=cands)
     if a.confirm_reps > 0:
         data = data or SuiteData(ctx, a.max_rows)
         summary["confirmed"] = confirm(data, ex, summary, reps=a.confirm_reps)

@@ -1,6 +1,6 @@
 """A small variant-selection suite end to end on the GPU: random queries of
 the three families, exhaustive timing, Algorithm 1 per family, and the cost
-model trained with its own kernels and judged on held-out queries."""
+model trained with its own kernels and assessed on held-out queries."""
 import math
 
 import pytest
@@ -30,7 +30,7 @@ def test_confirm_retimes_the_held_out_candidates():
     ctx = pv.Context(0)
     data = suite.SuiteData(ctx, 2_000_000)
     ex = suite.explore(ctx, 12, 2_000_000, 200_000, reps=2, log=None, data=data)
-    s = suite.judge(ctx, ex, candidates=((200, 1, 3e-3),))
+    s = suite.assess(ctx, ex, candidates=((200, 1, 3e-3),))
     c = suite.confirm(data, ex, s, reps=3, log=None)
     ctx.close()
     assert c["reps"] == 3 and len(c["per_query"]) == len(s["per_query"])
