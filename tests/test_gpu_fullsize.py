@@ -75,15 +75,20 @@ def _keyval_60m(ctx, g, dist):
 
 @pytest.mark.parametrize("g,dist,variants", [
     (1000, "uniform", [dict(agg="local", ht="perfect", pred="branch", items_per_thread=1, block=256, prefetch=1),
-                       dict(agg="local", ht="linear", items_per_thread=1)]),
+                       dict(agg="local", ht="linear", items_per_thread=1),
+                       dict(agg="cluster", ht="perfect", pred="branch", items_per_thread=1, block=512)]),
+    (10, "uniform", [dict(agg="local", ht="perfect", threads_per_table=1, pred="predicated", items_per_thread=1,
+                          block=256, prefetch=1),   # the benchmark's tuned variant for G = 10
+                     dict(agg="global", ht="perfect", pred="branch", items_per_thread=1, warp_agg=1)]),
     (1_000_000, "zipf", [dict(agg="global", ht="perfect", pred="branch", items_per_thread=1, block=256),
+                         dict(agg="global", ht="perfect", pred="branch", items_per_thread=1, block=256, warp_agg=1),
                          dict(agg="global", ht="cuckoo", exec="multi", items_per_thread=1)]),
 ])
 def test_keyval_60m_rows(ctx, g, dist, variants):
     host, keep = _keyval_60m(ctx, g, dist)
     plan = workloads.keyval_plan()
     w = _oracle(plan, host)
-    assert len(w[0]) <= g and int(w[2].sum()) == 60_000_000
+    assert len(w[0]) <= g and int(w[2].sum()) == 60_000_000  # COUNT of all rows
     for kw in variants:
         assert_same(ctx.query(plan, pv.variant(**kw)), w, ctxmsg=str(kw))
 
@@ -103,7 +108,27 @@ def test_star_join_60m_rows(ctx):
     plan = workloads.star_plan()
     w = _oracle(plan, host)
     assert len(w[0]) > 100
-    for kind, kw in (("perfect", dict(agg="local", ht="perfect", pred="branch", items_per_thread=1, block=512)),
+    for kind, kw in (("perfect", dict(agg="global", ht="perfect", pred="compacted", items_per_thread=1, block=512)),
+                     ("perfect", dict(agg="local", ht="perfect", pred="branch", items_per_thread=1, block=512)),
                      ("linear", dict(agg="global", ht="linear", pred="predicated", items_per_thread=1, prefetch=1)),
-                     ("cuckoo", dict(agg="local", ht="perfect", pred="branch", items_per_thread=1, block=256))):
+                     ("cuckoo", dict(agg="local", ht="linear", pred="compacted", items_per_thread=1, block=256))):
         assert_same(ctx.query(plan, pv.variant(**kw), pv.ht_variant(kind)), w, ctxmsg=f"{kind} {kw}")
+
+
+def test_filter_aggregate_compacted_100m_rows(ctx):
+    """The compacted filter/aggregate at 100M rows (the scale where it is the fastest variant),
+    against the oracle on the host cores."""
+    import torch
+    n = 100_000_000
+    u = datagen.uniform_int_torch
+    seed = datagen.DEFAULT_SEED
+    cols = {"a": u(seed, 101, n, 0, 100, torch.int32, device="cuda"),
+            "b": u(seed, 102, n, 0, 100, torch.int32, device="cuda"),
+            "price": u(seed, 103, n, 100, 10_000_000, torch.int64, device="cuda")}
+    ctx.register_table("t", cols)
+    host = {"t": {c: v.cpu().numpy() for c, v in cols.items()}}
+    plan = workloads.filter_agg_plan()
+    w = _oracle(plan, host)
+    for kw in (dict(pred="compacted", items_per_thread=1, block=256),
+               dict(pred="branch", items_per_thread=1, block=1024, prefetch=1)):
+        assert_same(ctx.query(plan, pv.variant(**kw)), w, ctxmsg=str(kw))
