@@ -62,7 +62,7 @@ TUNED = {
 }
 
 
-def make_tables(name: str, rows: int, groups: int):
+def make_tables(name: str, rows: int, groups: int, dist: str = "uniform"):
     if name == "lowcard":
         return {"li": datagen.table_lowcard_groups(rows)}, workloads.lowcard_plan()
     if name == "filter_agg":
@@ -70,7 +70,7 @@ def make_tables(name: str, rows: int, groups: int):
     if name == "filter_project":
         return {"t": datagen.table_filter_agg(rows)}, workloads.filter_project_plan()
     if name == "keyval":
-        return {"kv": datagen.table_keyval(rows, groups)}, workloads.keyval_plan()
+        return {"kv": datagen.table_keyval(rows, groups, dist)}, workloads.keyval_plan()
     if name == "star":
         s = datagen.star_schema(rows)
         return s, workloads.star_plan()
@@ -355,7 +355,7 @@ def run_reference(args):
         return 0
     w = WORKLOADS[args.workload]
     rows = args.rows or w["rows"]
-    tables, plan = make_tables(args.workload, rows, args.groups)
+    tables, plan = make_tables(args.workload, rows, args.groups, args.dist)
     from oracle import oracle
     cores = args.cpu_threads or oracle.hardware_threads()
     for _ in range(args.warmup):
@@ -390,7 +390,7 @@ def run_pv(args):
     torch.cuda.set_device(local)
     w = WORKLOADS[args.workload]
     rows = args.rows or w["rows"]
-    tables, plan = make_tables(args.workload, rows, args.groups)
+    tables, plan = make_tables(args.workload, rows, args.groups, args.dist)
     ctx = pv.Context(local)
     dev = {t: {c: torch.from_numpy(np.ascontiguousarray(v)).cuda(local) for c, v in cols.items()}
            for t, cols in tables.items()}
@@ -491,7 +491,9 @@ def run_pv(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000 * total_s / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic (seeded counter-based generator)",
-        "config": {"workload": w["desc"], "rows": rows, "variant": dict(var_kw, build=build_ht),
+        "config": {"workload": w["desc"], "rows": rows,
+                   **({"groups": args.groups, "keys": args.dist} if args.workload == "keyval" else {}),
+                   "variant": dict(var_kw, build=build_ht),
                    "tuning": tuning,
                    "l2": ("hot: no flush between steps, the inputs stay in L2 (hot-L2 numbers)" if args.hot_l2 else
                           "flushed (2x L2 write, then discard) before every step, outside the timed events"),
@@ -539,6 +541,7 @@ def main():
     ap.add_argument("--workload", default="lowcard", choices=sorted(WORKLOADS))
     ap.add_argument("--rows", type=int, default=0)
     ap.add_argument("--groups", type=int, default=1000)
+    ap.add_argument("--dist", default="uniform", choices=["uniform", "zipf"], help="keyval: key distribution")
     ap.add_argument("--variant", default="", help="JSON pv_variant fields (skips tuning)")
     ap.add_argument("--no-tune", action="store_true", help="use the built-in variant instead of tuning")
     ap.add_argument("--build-ht", default="perfect")

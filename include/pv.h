@@ -136,8 +136,9 @@ typedef struct {
 
 /* Variant configuration (Section 3.3, 4, 6; Table 5's dimensions). */
 typedef enum { PV_EXEC_SINGLE_PASS = 0, PV_EXEC_MULTI_PASS = 1 } pv_exec;
-/* PV_AGG_CLUSTER (perfect tables): the table is partitioned over the shared memory of the 8 CTAs of a
- * thread-block cluster and updated with cluster-scope atomics, then merged into the global table. */
+/* PV_AGG_CLUSTER (perfect tables): the table is partitioned over the shared memory of the CTAs of a
+ * thread-block cluster (the smallest power of two, 2..16, whose part fits) and updated with
+ * cluster-scope atomics, then merged into the global table. */
 typedef enum { PV_AGG_LOCAL = 0, PV_AGG_GLOBAL = 1, PV_AGG_CLUSTER = 2 } pv_agg_strategy;
 /* PV_COMPACTED (grouped pipelines): branched first operation (the filters, else the
  * first probe); its surviving rows are queued per warp and run one per lane through

@@ -314,11 +314,12 @@ struct SinkLocalPerfect {
   }
 };
 
-// Perfect array partitioned over the CTAs of a thread-block cluster
-// (distributed shared memory): slot s lives in CTA s mod kClusterCTAs of the
-// cluster, at local slot s / kClusterCTAs, so a cluster keeps kClusterCTAs
-// times the domain one CTA could on chip, and neighbouring (often equally
-// hot) slots spread over its CTAs.  Rows update the owner's words with
+// Perfect array partitioned over the C = 2^g.cluster_log2 CTAs of a
+// thread-block cluster (distributed shared memory): slot s lives in CTA
+// s mod C of the cluster, at local slot s / C, so a cluster keeps C times the
+// domain one CTA could on chip, and neighbouring (often equally hot) slots
+// spread over its CTAs.  The host picks the smallest C (2..16) whose part
+// fits in shared memory.  Rows update the owner's words with
 // cluster-scope shared-memory atomics: sums as two 32-bit fetch-adds (the
 // high word only on a carry or a non-zero high part, as shared_add64), MIN /
 // MAX codes with a 64-bit compare-and-swap loop.  Prologue: zero the local part, cluster
@@ -326,7 +327,7 @@ struct SinkLocalPerfect {
 // (every update has landed), then each CTA merges its part into the global
 // table with one atomic per non-zero word.  Every thread of every CTA of the
 // cluster reaches both barriers.
-constexpr int kClusterCTAs = 8;
+constexpr int kMaxClusterCTAs = 16;
 
 // Cluster-wide barrier (not .aligned: the threads of a warp may reach it
 // diverged, e.g. after a grid-stride loop).
@@ -381,13 +382,13 @@ template <class SH>
 struct SinkClusterPerfect {
   static constexpr int NA = SH::Aggs::N;
   static constexpr bool kCluster = true;
-  static __host__ __device__ int64_t part_slots(int64_t cap) { return (cap + kClusterCTAs - 1) / kClusterCTAs; }
+  static __host__ __device__ int64_t part_slots(int64_t cap, int log2c) { return (cap + (1 << log2c) - 1) >> log2c; }
   const GroupDesc& gd; const GroupOut& g; int32_t* err; unsigned long long* sm;
   uint32_t sbase, rank;
   __device__ SinkClusterPerfect(const GroupDesc& d, const GroupOut& o, int32_t* e, unsigned long long* s)
       : gd(d), g(o), err(e), sm(s), sbase(static_cast<uint32_t>(__cvta_generic_to_shared(s))), rank(cluster_rank()) {}
   __device__ void init() {
-    const int64_t words = part_slots(g.cap) * g.stride;
+    const int64_t words = part_slots(g.cap, g.cluster_log2) * g.stride;
     for (int64_t i = threadIdx.x; i < words; i += blockDim.x) sm[i] = 0;
     cluster_sync();
   }
@@ -402,8 +403,8 @@ struct SinkClusterPerfect {
     row_codes<SH>(it, kp, r, live ? ~0ull : 0ull, c);
     if (g.warp_agg && !warp_preaggregate<SH>(s, c)) return;
     const uint32_t base = cluster_map(
-        sbase + static_cast<uint32_t>(s / kClusterCTAs) * static_cast<uint32_t>(g.stride) * 8u,
-        static_cast<uint32_t>(s % kClusterCTAs));
+        sbase + static_cast<uint32_t>(s >> g.cluster_log2) * static_cast<uint32_t>(g.stride) * 8u,
+        static_cast<uint32_t>(s & ((1u << g.cluster_log2) - 1u)));
     using A = typename SH::Aggs;
     static_for<NA + 1>([&](auto a) {
       constexpr int I = decltype(a)::value;
@@ -417,11 +418,11 @@ struct SinkClusterPerfect {
   }
   __device__ void finish() {
     cluster_sync();
-    const int64_t words = part_slots(g.cap) * g.stride;
+    const int64_t words = part_slots(g.cap, g.cluster_log2) * g.stride;
     for (int64_t i = threadIdx.x; i < words; i += blockDim.x) {
       const uint64_t v = sm[i];
       if (!v) continue;
-      const int64_t slot = (i / g.stride) * kClusterCTAs + rank;
+      const int64_t slot = ((i / g.stride) << g.cluster_log2) + rank;
       const int a = static_cast<int>(i % g.stride);
       if (slot >= g.cap) continue;
       unsigned long long* dst = g.vals + (blockIdx.x % g.replicas) * g.rep_stride + slot * g.stride + a;
@@ -833,20 +834,25 @@ static pv_status run_group_compact(const LaunchCfg& c, const KParams& kp, const 
   }
 }
 
-// Launch as clusters of kClusterCTAs CTAs: the grid is the co-resident
-// clusters times kClusterCTAs (or grid_mult x SMs rounded down to whole
+// Launch as clusters of C = 2^g.cluster_log2 CTAs: the grid is the
+// co-resident clusters times C (or grid_mult x SMs rounded down to whole
 // clusters), unsupported when no cluster of this kernel fits.
 template <class K>
 static pv_status launch_k_cluster(const LaunchCfg& c, K k, const KParams& kp, const GroupDesc& gd,
                                   const GroupOut& g, size_t smem) {
+  const int cl = 1 << g.cluster_log2;
   if (smem > 48 * 1024) {
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
       return PV_ERR_UNSUPPORTED;
   }
+  if (cl > 8 && cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    cudaGetLastError();
+    return PV_ERR_UNSUPPORTED;
+  }
   cudaLaunchConfig_t cfg{};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = kClusterCTAs;
+  attr[0].val.clusterDim.x = cl;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.blockDim = dim3(c.block);
@@ -854,15 +860,15 @@ static pv_status launch_k_cluster(const LaunchCfg& c, K k, const KParams& kp, co
   cfg.stream = c.stream;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cfg.gridDim = dim3(kClusterCTAs);
+  cfg.gridDim = dim3(cl);
   int clusters = 0;
   if (cudaOccupancyMaxActiveClusters(&clusters, k, &cfg) != cudaSuccess || clusters <= 0) {
     cudaGetLastError();
     return PV_ERR_UNSUPPORTED;
   }
-  int64_t grid = c.grid_mult > 0 ? (static_cast<int64_t>(c.grid_mult) * c.sm_count) / kClusterCTAs * kClusterCTAs
-                                 : static_cast<int64_t>(clusters) * kClusterCTAs;
-  grid = std::max<int64_t>(kClusterCTAs, std::min<int64_t>(grid, static_cast<int64_t>(clusters) * kClusterCTAs));
+  int64_t grid = c.grid_mult > 0 ? (static_cast<int64_t>(c.grid_mult) * c.sm_count) / cl * cl
+                                 : static_cast<int64_t>(clusters) * cl;
+  grid = std::max<int64_t>(cl, std::min<int64_t>(grid, static_cast<int64_t>(clusters) * cl));
   cfg.gridDim = dim3(static_cast<unsigned>(grid));
   kmark(c);
   const cudaError_t e = cudaLaunchKernelEx(&cfg, k, kp, gd, g);
@@ -929,8 +935,16 @@ static pv_status launch_group(const LaunchCfg& c, const KParams& kp, const Group
   if (v.agg != PV_AGG_LOCAL && v.agg != PV_AGG_GLOBAL && v.agg != PV_AGG_CLUSTER) return PV_ERR_INVALID_ARG;
   if (v.agg == PV_AGG_CLUSTER) {  // perfect arrays in the distributed shared memory of a cluster
     if (g.ht != PV_HT_PERFECT || multi || v.threads_per_table == 1) return PV_ERR_UNSUPPORTED;
-    const size_t smem = static_cast<size_t>(SinkClusterPerfect<SH>::part_slots(g.cap)) * g.stride * 8;
+    // the smallest cluster (2..16 CTAs) whose part fits: fewer CTAs keep more updates local (8 CTAs with
+    // 150 KB parts measured faster than 16 with 75 KB on 5e4 skewed groups)
+    int l = 1;
+    auto part_bytes = [&](int lg) {
+      return static_cast<size_t>(SinkClusterPerfect<SH>::part_slots(g.cap, lg)) * g.stride * 8;
+    };
+    while ((1 << l) < kMaxClusterCTAs && part_bytes(l) > kClusterBytes) ++l;
+    const size_t smem = part_bytes(l);
     if (smem > kClusterBytes) return PV_ERR_UNSUPPORTED;
+    g.cluster_log2 = l;
     const pv_status s = run_group<SH, UMASK, SinkClusterPerfect>(c, kp, gd, g, smem);
     if (s != PV_OK) return s;
     return launch_dedupe_extract(c, gd, g, false);

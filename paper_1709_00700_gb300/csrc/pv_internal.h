@@ -116,6 +116,7 @@ struct GroupOut {
   // Perfect tables of few slots are replicated: CTA b adds into replica
   // b % replicas (vals + replica * rep_stride), which spreads the atomics of
   // many CTAs on the same few words; extraction folds the replicas.
+  int cluster_log2;   // cluster tables: log2 of the CTAs per cluster (the table's partitions)
   int replicas;       // 1 for hashed tables
   int64_t rep_stride; // words between replicas: (cap + 1) * stride
   // Extraction (dense result columns, int64): out[c * out_cap + row].
