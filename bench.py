@@ -49,6 +49,10 @@ WORKLOADS = {
                    desc="SUM(val), COUNT(*) GROUP BY key, 60M rows, G groups"),
     "star": dict(rows=60_000_000, bytes_per_row=24,
                  desc="four-probe star join grouped on two dimension attributes, 60M fact rows"),
+    "keys3": dict(rows=60_000_000, bytes_per_row=3 * 4 + 8,
+                  desc="SUM(val), COUNT(*) GROUP BY a, b, c (16 x 64 x 7 groups), 60M rows"),
+    "star3": dict(rows=60_000_000, bytes_per_row=3 * 4 + 8,
+                  desc="three-probe star join (SSB Q3.1 shape) grouped on three dimension attributes, 60M fact rows"),
 }
 
 # Variant per workload (measured best so far; the autotuner refreshes these).
@@ -59,6 +63,9 @@ TUNED = {
     "filter_project": dict(exec="single", pred="branch", access="grid", items_per_thread=4, block=128),
     "keyval": dict(agg="local", ht="perfect", pred="branch", access="grid", items_per_thread=1, block=512),
     "star": dict(agg="global", ht="perfect", pred="compacted", access="grid", items_per_thread=1, block=512),
+    "keys3": dict(agg="cluster", ht="perfect", pred="branch", access="grid", items_per_thread=1, block=512,
+                  warp_agg=1),
+    "star3": dict(agg="global", ht="perfect", pred="compacted", access="grid", items_per_thread=1, block=512),
 }
 
 
@@ -74,11 +81,15 @@ def make_tables(name: str, rows: int, groups: int, dist: str = "uniform"):
     if name == "star":
         s = datagen.star_schema(rows)
         return s, workloads.star_plan()
+    if name == "keys3":
+        return {"k3": datagen.table_keys3(rows)}, workloads.keys3_plan()
+    if name == "star3":
+        return datagen.star3_schema(rows), workloads.star3_plan()
     raise ValueError(name)
 
 
 TUNE_GRID = {"lowcard": "grouped", "keyval": "grouped", "filter_agg": "filter_aggregate",
-             "filter_project": "filter_project", "star": "star"}
+             "filter_project": "filter_project", "star": "star", "keys3": "grouped", "star3": "star"}
 
 
 def tune(ctx, plan, name, reps=3):
@@ -465,7 +476,7 @@ def run_pv(args):
     peak, peak_kind = measured_peaks()
     alg_bytes = w["bytes_per_row"] * rows
     upper_bytes = None
-    if args.workload == "star":
+    if args.workload in ("star", "star3"):
         upper_bytes, alg_bytes = alg_bytes, star_sector_bytes(tables, plan)
     achieved = alg_bytes / (dom_ms / 1000.0) / 1e9
     # end to end through the C ABI with host buffers: H2D of the step's input

@@ -62,7 +62,7 @@ typedef int32_t pv_graph; /* captured-graph handle */
 
 #define PV_MAX_PREDS 4
 #define PV_MAX_PROBES 4
-#define PV_MAX_KEYS 2
+#define PV_MAX_KEYS 3
 #define PV_MAX_AGGS 8
 #define PV_MAX_TERMS 3
 #define PV_MAX_PROJ 4
@@ -118,7 +118,12 @@ typedef struct {
  *   n_proj > 0              PROJECT proj (n_aggs must be 0)
  *   n_keys > 0              HASH_AGGREGATE(keys, aggs)
  *   otherwise               AGGREGATE(aggs)
- * All fact columns referenced must have the same row count. */
+ * All fact columns referenced must have the same row count.
+ * Group keys (the attribute set G of HASH_AGGREGATE, Table 1): one part of any
+ * column type; two 32-bit parts (packed into one 64-bit key); or three parts
+ * (a composite key: each part minus its minimum, in mixed radix over the
+ * parts' value spans taken from column or build-payload statistics; the
+ * product of the spans must be at most 2^40, else PV_ERR_UNSUPPORTED). */
 typedef struct {
   int32_t n_preds;
   pv_pred preds[PV_MAX_PREDS];

@@ -27,13 +27,49 @@ constexpr int kLocalProbe = 16;          // probe-length bound in a local table
 constexpr size_t kLocalBytes = 96 << 10; // shared memory of a CTA-local table
 constexpr size_t kClusterBytes = 192 << 10;  // shared memory of one CTA's part of a cluster table
 
-__device__ __forceinline__ uint64_t perfect_index(const GroupDesc& gd, int64_t p0, int64_t p1, bool& ok) {
-  const int64_t a = p0 - gd.key_min[0];
-  ok = static_cast<uint64_t>(a) < static_cast<uint64_t>(gd.key_span[0]);
-  if (gd.n_keys == 1) return static_cast<uint64_t>(a);
-  const int64_t b = p1 - gd.key_min[1];
-  ok = ok && static_cast<uint64_t>(b) < static_cast<uint64_t>(gd.key_span[1]);
-  return static_cast<uint64_t>(a) * static_cast<uint64_t>(gd.key_span[1]) + static_cast<uint64_t>(b);
+// Whether every group-key part is a 32-bit source.
+template <class SH, int... I>
+constexpr bool key_parts32(std::integer_sequence<int, I...>) {
+  return (KeyPart32<SH, typename At<I, typename SH::Key::L>::type>::value && ...);
+}
+template <class SH>
+constexpr bool key_narrow() {
+  return key_parts32<SH>(std::make_integer_sequence<int, SH::Key::N>{});
+}
+
+// Mixed-radix code of row r's group key: each part minus its minimum, row-
+// major over the part spans (the last part varies fastest).  It is the
+// perfect-array slot and, for keys of three parts, the hash-table key.  ok is
+// false when a part lies outside its span (unsigned differences wrap below
+// the minimum).  Without WIDE, keys of 32-bit parts use 32-bit arithmetic:
+// a perfect array has at most 2^28 slots.
+template <class SH, bool WIDE = !key_narrow<SH>()>
+__device__ __forceinline__ uint64_t row_perfect_index(const GroupDesc& gd, Item<SH>& it, const KParams& kp, int r,
+                                                      bool& ok) {
+  using U = std::conditional_t<WIDE, uint64_t, uint32_t>;
+  U code = 0;
+  ok = true;
+  static_for<SH::Key::N>([&](auto p) {
+    constexpr int P = decltype(p)::value;
+    const U a = static_cast<U>(key_part<SH, P>(it, kp, r)) - static_cast<U>(gd.key_min[P]);
+    ok = ok && a < static_cast<U>(gd.key_span[P]);
+    code = P == 0 ? a : code * static_cast<U>(gd.key_span[P]) + a;
+  });
+  return code;
+}
+
+// Hash-table key of row r: the packed key for one or two parts, the mixed-
+// radix code for three (0, an in-domain code, when ok is false, so that rows
+// outside the domain add no keys).
+template <class SH>
+__device__ __forceinline__ uint64_t group_key(const GroupDesc& gd, Item<SH>& it, const KParams& kp, int r, bool& ok) {
+  if constexpr (SH::Key::N <= 2) {
+    ok = true;
+    return pack_key<SH>(it, kp, r);
+  } else {
+    const uint64_t code = row_perfect_index<SH, true>(gd, it, kp, r, ok);
+    return ok ? code : 0;
+  }
 }
 
 // Global linear probing: slot of key, inserting it if absent.  Returns
@@ -217,9 +253,11 @@ struct SinkGlobalHash {
   __device__ SinkGlobalHash(const GroupDesc& d, const GroupOut& o, int32_t* e, unsigned long long*) : gd(d), g(o), err(e) {}
   __device__ void init() {}
   __device__ __forceinline__ void add(Item<SH>& it, const KParams& kp, int r, bool live) {
-    const uint64_t key = pack_key<SH>(it, kp, r);
+    bool in_domain;
+    const uint64_t key = group_key<SH>(gd, it, kp, r, in_domain);
+    if (!in_domain && live) set_error(err, PV_ERR_KEY_OUT_OF_RANGE);
     uint64_t c[NA + 1];
-    row_codes<SH>(it, kp, r, live ? ~0ull : 0ull, c);
+    row_codes<SH>(it, kp, r, live && in_domain ? ~0ull : 0ull, c);
     if (g.warp_agg && !warp_preaggregate<SH>(key, c)) return;
     const uint64_t s = global_slot<GM>(g, key, err);
     if (s > static_cast<uint64_t>(g.cap)) return;
@@ -227,33 +265,6 @@ struct SinkGlobalHash {
   }
   __device__ void finish() {}
 };
-
-// Perfect-array slot of row r: parts minus their minima, row-major over the
-// part spans.  Keys made of 32-bit sources use 32-bit arithmetic (the domain
-// is at most 2^28 slots); unsigned differences wrap below the minimum.
-template <class SH>
-__device__ __forceinline__ uint64_t row_perfect_index(const GroupDesc& gd, Item<SH>& it, const KParams& kp, int r,
-                                                      bool& ok) {
-  using K = typename SH::Key;
-  constexpr bool narrow = KeyPart32<SH, typename At<0, typename K::L>::type>::value &&
-                          (K::N == 1 || KeyPart32<SH, typename At<K::N - 1, typename K::L>::type>::value);
-  if constexpr (narrow) {
-    const uint32_t a = static_cast<uint32_t>(key_part<SH, 0>(it, kp, r)) - static_cast<uint32_t>(gd.key_min[0]);
-    ok = a < static_cast<uint32_t>(gd.key_span[0]);
-    if constexpr (K::N == 1) {
-      return a;
-    } else {
-      const uint32_t b = static_cast<uint32_t>(key_part<SH, 1>(it, kp, r)) - static_cast<uint32_t>(gd.key_min[1]);
-      ok = ok && b < static_cast<uint32_t>(gd.key_span[1]);
-      return a * static_cast<uint32_t>(gd.key_span[1]) + b;
-    }
-  } else {
-    const int64_t p0 = key_part<SH, 0>(it, kp, r);
-    int64_t p1 = 0;
-    if constexpr (K::N == 2) p1 = key_part<SH, 1>(it, kp, r);
-    return perfect_index(gd, p0, p1, ok);
-  }
-}
 
 template <class SH>
 struct SinkGlobalPerfect {
@@ -545,9 +556,11 @@ struct SinkLocalHash {
     __syncthreads();
   }
   __device__ __forceinline__ void add(Item<SH>& it, const KParams& kp, int r, bool live) {
-    const uint64_t key = pack_key<SH>(it, kp, r);
+    bool in_domain;
+    const uint64_t key = group_key<SH>(gd, it, kp, r, in_domain);
+    if (!in_domain && live) set_error(err, PV_ERR_KEY_OUT_OF_RANGE);
     uint64_t c[NA + 1];
-    row_codes<SH>(it, kp, r, live ? ~0ull : 0ull, c);
+    row_codes<SH>(it, kp, r, live && in_domain ? ~0ull : 0ull, c);
     if (key != kEmpty64) {
       const uint32_t mask = static_cast<uint32_t>(g.local_slots) - 1;
       uint32_t idx = static_cast<uint32_t>(fmix64(key)) & mask;
@@ -589,6 +602,25 @@ __device__ __forceinline__ int64_t decode_agg(int func, uint64_t c) {
   return static_cast<int64_t>(c);
 }
 
+// Key columns of result row pos.  code: v is a mixed-radix slot code (perfect
+// arrays, keys of three parts), decoded part by part from the last; else v is
+// a packed hash key (one part, or two 32-bit halves).
+__device__ __forceinline__ void write_keys(const GroupDesc& gd, const GroupOut& g, int64_t pos, bool code, uint64_t v) {
+  if (code) {
+    for (int i = gd.n_keys - 1; i > 0; --i) {
+      const uint64_t span = static_cast<uint64_t>(gd.key_span[i]);
+      g.out[i * g.out_cap + pos] = gd.key_min[i] + static_cast<int64_t>(v % span);
+      v /= span;
+    }
+    g.out[pos] = gd.key_min[0] + static_cast<int64_t>(v);
+  } else if (gd.n_keys == 1) {
+    g.out[pos] = gd.key64[0] ? static_cast<int64_t>(v) : static_cast<int64_t>(static_cast<int32_t>(static_cast<uint32_t>(v)));
+  } else {
+    g.out[pos] = static_cast<int32_t>(static_cast<uint32_t>(v >> 32));
+    g.out[g.out_cap + pos] = static_cast<int32_t>(static_cast<uint32_t>(v));
+  }
+}
+
 __device__ __forceinline__ void extract_slots(const GroupDesc& gd, const GroupOut& g, int64_t t, int64_t T) {
   const int64_t total = g.cap + 1;
   const int lane = threadIdx.x & 31;
@@ -618,22 +650,7 @@ __device__ __forceinline__ void extract_slots(const GroupDesc& gd, const GroupOu
     if (occ) {
       const int64_t pos = static_cast<int64_t>(base) + __popc(ball & ((1u << lane) - 1u));
       if (pos < g.out_cap) {
-        int64_t k0, k1 = 0;
-        if (perfect) {
-          if (gd.n_keys == 1) {
-            k0 = gd.key_min[0] + s;
-          } else {
-            k0 = gd.key_min[0] + s / gd.key_span[1];
-            k1 = gd.key_min[1] + s % gd.key_span[1];
-          }
-        } else if (gd.n_keys == 1) {
-          k0 = gd.key64[0] ? static_cast<int64_t>(key) : static_cast<int64_t>(static_cast<int32_t>(static_cast<uint32_t>(key)));
-        } else {
-          k0 = static_cast<int32_t>(static_cast<uint32_t>(key >> 32));
-          k1 = static_cast<int32_t>(static_cast<uint32_t>(key));
-        }
-        g.out[pos] = k0;
-        if (gd.n_keys == 2) g.out[g.out_cap + pos] = k1;
+        write_keys(gd, g, pos, perfect || gd.n_keys > 2, perfect ? static_cast<uint64_t>(s) : key);
         for (int a = 0; a < na; ++a) g.out[(gd.n_keys + a) * g.out_cap + pos] = decode_agg(gd.func[a], __ldcg(v + a));
       }
     }
@@ -667,12 +684,7 @@ __device__ __forceinline__ void extract_replicated(const GroupDesc& gd, const Gr
     if (lane == 0) {
       const int64_t pos = static_cast<int64_t>(atomicAdd(g.out_count, 1ull));
       if (pos < g.out_cap) {
-        if (gd.n_keys == 1) {
-          g.out[pos] = gd.key_min[0] + s;
-        } else {
-          g.out[pos] = gd.key_min[0] + s / gd.key_span[1];
-          g.out[g.out_cap + pos] = gd.key_min[1] + s % gd.key_span[1];
-        }
+        write_keys(gd, g, pos, true, static_cast<uint64_t>(s));
         for (int a = 0; a < na; ++a) g.out[(gd.n_keys + a) * g.out_cap + pos] = decode_agg(gd.func[a], w[a]);
       }
     }
@@ -783,7 +795,9 @@ __global__ void __maxnreg__(128) k_group_keys(const __grid_constant__ KParams kp
       for (int r = 0; r < 4; ++r) {
         const bool live = (it[u].mask >> r) & 1u;
         if (PRED ? r < it[u].nvalid : live) {
-          const uint64_t key = pack_key<SH>(it[u], kp, r);
+          bool in_domain;
+          const uint64_t key = group_key<SH>(gd, it[u], kp, r, in_domain);
+          if (!in_domain && live) set_error(kp.err, PV_ERR_KEY_OUT_OF_RANGE);
           if constexpr (HTK == PV_HT_CUCKOO) global_cuckoo_insert(g, key, kp.err);
           else global_linear_slot(g, key, kp.err);
         }

@@ -49,6 +49,8 @@ void register_group_keyval_f();
 void register_group_star();
 void register_group_join2();
 void register_group_join2y();
+void register_group_keys3();
+void register_group_star3();
 
 void register_group_shapes() {
   register_group_lowcard();
@@ -57,6 +59,8 @@ void register_group_shapes() {
   register_group_star();
   register_group_join2();
   register_group_join2y();
+  register_group_keys3();
+  register_group_star3();
 }
 
 }  // namespace pv

@@ -618,6 +618,8 @@ static pv_status alloc_result(pv_ctx* c, Result& r) {
       domain *= gd.key_span[i];
     else domain_ok = false;
   }
+  if (k.n_keys > 2 && !domain_ok)
+    return fail(c, PV_ERR_UNSUPPORTED, "three-part group keys need a key domain of at most 2^40 codes");
   GroupOut& g = r.grp;
   g.ht = r.var.ht;
   g.hash = r.var.hash;

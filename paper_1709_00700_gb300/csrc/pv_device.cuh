@@ -510,6 +510,7 @@ template <class SH, int S> struct KeyPart32<SH, X<S>>
 template <class SH>
 __device__ __forceinline__ uint64_t pack_key(Item<SH>& it, const KParams& kp, int r) {
   using K = typename SH::Key;
+  static_assert(K::N <= 2, "keys of three parts are mixed-radix codes over the part domains");
   if constexpr (K::N == 1) {
     using K0 = typename At<0, typename K::L>::type;
     const int64_t v = TermEval<K0>::get(it, kp, r);

@@ -222,6 +222,46 @@ def star_schema(n: int = 60_000_000, seed: int = DEFAULT_SEED) -> dict:
     return {"fact": star_fact(n, seed), **dims}
 
 
+def table_keys3(n: int, spans=(16, 64, 7), lows=(0, 0, 1992), seed: int = DEFAULT_SEED) -> dict:
+    """Composite-key table: a, b, c int32 uniform over [low_i, low_i + span_i),
+    val int64 uniform over [0, 1e6)."""
+    t = {name: uniform_int(seed, 311 + i, n, lo, lo + sp, np.int32)
+         for i, (name, lo, sp) in enumerate(zip("abc", lows, spans))}
+    t["val"] = uniform_int(seed, 314, n, 0, 1_000_000, np.int64)
+    return t
+
+
+# Three-dimension star schema of the SSB Q3 flight: customer and supplier
+# tables carry a nation (25 values) and its region (nation // 5, 5 values), the
+# date table one row per day of 7 years with its year.  Row counts are those
+# of SSB at scale factor 1 (30,000 customers, 2,000 suppliers, 2,556 days).
+STAR3_DIMS = (("d_cust", 30_000), ("d_supp", 2_000), ("d_date", 2_556))
+STAR3_YEAR0 = 1992
+
+
+def star3_dimension(name: str, seed: int = DEFAULT_SEED) -> dict:
+    idx = [d[0] for d in STAR3_DIMS].index(name)
+    rows = STAR3_DIMS[idx][1]
+    r = np.arange(rows, dtype=np.int64)
+    key = ((r * coprime_multiplier(rows, 7919) + 17) % rows).astype(np.int32)
+    if name == "d_date":
+        year = (STAR3_YEAR0 + np.minimum(r // 365, 6)).astype(np.int32)
+        return {"key": key, "year": year}
+    nation = uniform_int(seed, 601 + idx, rows, 0, 25, np.int32)
+    return {"key": key, "nation": nation, "region": (nation // 5).astype(np.int32)}
+
+
+def star3_fact(n: int, seed: int = DEFAULT_SEED) -> dict:
+    t = {"fk_" + name[2:]: uniform_int(seed, 611 + j, n, 0, rows, np.int32)
+         for j, (name, rows) in enumerate(STAR3_DIMS)}
+    t["revenue"] = uniform_int(seed, 619, n, 100, 10_000_000, np.int64)
+    return t
+
+
+def star3_schema(n: int = 60_000_000, seed: int = DEFAULT_SEED) -> dict:
+    return {"fact": star3_fact(n, seed), **{name: star3_dimension(name, seed) for name, _ in STAR3_DIMS}}
+
+
 # ---------------------------------------------------------------------------
 # The same streams computed with torch (on any device), bit-identical to the
 # numpy definitions above.  uint64 arithmetic is carried in int64 tensors:

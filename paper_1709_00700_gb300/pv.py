@@ -23,7 +23,7 @@ STATUS = {0: "PV_OK", -1: "PV_ERR_INVALID_ARG", -2: "PV_ERR_UNSUPPORTED", -3: "P
           -4: "PV_ERR_CUCKOO_CYCLE", -5: "PV_ERR_KEY_OUT_OF_RANGE", -6: "PV_ERR_DUP_BUILD_KEY",
           -7: "PV_ERR_OUTPUT_OVERFLOW", -8: "PV_ERR_TIMEOUT", -9: "PV_ERR_CUDA", -10: "PV_ERR_OOM"}
 PV_I32, PV_I64, PV_U8 = 0, 1, 2
-MAX_PREDS, MAX_PROBES, MAX_KEYS, MAX_AGGS, MAX_TERMS, MAX_PROJ, MAX_PAYLOAD = 4, 4, 2, 8, 3, 4, 1
+MAX_PREDS, MAX_PROBES, MAX_KEYS, MAX_AGGS, MAX_TERMS, MAX_PROJ, MAX_PAYLOAD = 4, 4, 3, 8, 3, 4, 1
 OPS = {"lt": 0, "le": 1, "gt": 2, "ge": 3, "eq": 4, "between": 5}
 FUNCS = {"sum": 0, "count": 1, "min": 2, "max": 3}
 TERMS = {"x": 0, "x_plus_c": 1, "c_minus_x": 2}

@@ -73,3 +73,27 @@ def star_plan(thresholds: dict | None = None, order=STAR_PROBE_ORDER) -> dict:
     return {"fact": "fact", "builds": builds, "probes": probes,
             "group_by": [["payload", ia, 0], ["payload", ib, 0]],
             "aggs": [["sum", [["x", "revenue"]]], ["count"]]}
+
+
+# Grouped aggregation on a composite key of three fact columns:
+# SUM(val), COUNT(*) GROUP BY a, b, c.
+def keys3_plan() -> dict:
+    return {"fact": "k3", "group_by": ["a", "b", "c"], "aggs": [["sum", [["x", "val"]]], ["count"]]}
+
+
+# Star join shaped like SSB Q3.1: customers and suppliers of one region, the
+# years [year_lo, year_hi]; probes in that order (most selective first);
+# SUM(revenue) GROUP BY customer nation, supplier nation, year.
+STAR3_REGIONS = (2, 2)
+STAR3_YEARS = (datagen.STAR3_YEAR0, datagen.STAR3_YEAR0 + 5)
+
+
+def star3_plan(regions=STAR3_REGIONS, years=STAR3_YEARS) -> dict:
+    builds = [{"table": "d_cust", "key": "key", "filters": [["region", "eq", regions[0]]], "payload": ["nation"]},
+              {"table": "d_supp", "key": "key", "filters": [["region", "eq", regions[1]]], "payload": ["nation"]},
+              {"table": "d_date", "key": "key", "filters": [["year", "between", years[0], years[1]]],
+               "payload": ["year"]}]
+    return {"fact": "fact", "builds": builds,
+            "probes": [{"build": 0, "fk": "fk_cust"}, {"build": 1, "fk": "fk_supp"}, {"build": 2, "fk": "fk_date"}],
+            "group_by": [["payload", 0, 0], ["payload", 1, 0], ["payload", 2, 0]],
+            "aggs": [["sum", [["x", "revenue"]]]]}

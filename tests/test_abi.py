@@ -52,3 +52,35 @@ def test_library_fails_loudly_when_missing(tmp_path):
         pv._lib = None
         pv.load(str(tmp_path / "libpv.so"))
     pv._lib = None
+
+
+def _c_layout(tmp_path, structs):
+    """sizeof and offsetof of every field of the given structs, as the C
+    compiler lays them out from include/pv.h."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "pv.h"', "int main(void) {"]
+    for name, st in structs.items():
+        lines.append(f'  printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for f, _ in st._fields_:
+            lines.append(f'  printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    return {tuple(l.split()[:2]): int(l.split()[2]) for l in out.splitlines()}
+
+
+def test_binding_layout_matches_the_c_compiler(tmp_path):
+    structs = {n: getattr(pv, n) for n in ("pv_ref", "pv_pred", "pv_term", "pv_agg", "pv_probe", "pv_build_spec",
+                                           "pv_ht_variant", "pv_pipeline_spec", "pv_variant")}
+    c = _c_layout(tmp_path, structs)
+    for name, st in structs.items():
+        assert c[(name, "sizeof")] == ctypes.sizeof(st), name
+        for f, _ in st._fields_:
+            assert c[(name, f)] == getattr(st, f).offset, (name, f)

@@ -132,3 +132,45 @@ def test_filter_aggregate_compacted_100m_rows(ctx):
     for kw in (dict(pred="compacted", items_per_thread=1, block=256),
                dict(pred="branch", items_per_thread=1, block=1024, prefetch=1)):
         assert_same(ctx.query(plan, pv.variant(**kw)), w, ctxmsg=str(kw))
+
+
+def test_three_part_keys_60m_rows(ctx):
+    import torch
+    n = 60_000_000
+    seed = datagen.DEFAULT_SEED
+    u = datagen.uniform_int_torch
+    cols = {name: u(seed, 311 + i, n, lo, lo + sp, torch.int32, device="cuda")
+            for i, (name, lo, sp) in enumerate(zip("abc", (0, 0, 1992), (16, 64, 7)))}
+    cols["val"] = u(seed, 314, n, 0, 1_000_000, torch.int64, device="cuda")
+    ctx.register_table("k3", cols)
+    host = {"k3": {c: v.cpu().numpy() for c, v in cols.items()}}
+    plan = workloads.keys3_plan()
+    w = _oracle(plan, host)
+    assert len(w[0]) == 16 * 64 * 7 and int(w[4].sum()) == n
+    for kw in (dict(agg="cluster", ht="perfect", pred="branch", items_per_thread=1, block=512, warp_agg=1),
+               dict(agg="global", ht="perfect", pred="predicated", items_per_thread=1, block=256),
+               dict(agg="global", ht="linear", pred="predicated", items_per_thread=1, warp_agg=1),
+               dict(agg="local", ht="cuckoo", exec="multi", items_per_thread=1)):
+        assert_same(ctx.query(plan, pv.variant(**kw)), w, ctxmsg=str(kw))
+
+
+def test_star3_60m_rows(ctx):
+    import torch
+    n = 60_000_000
+    dims = {name: datagen.star3_dimension(name) for name, _ in datagen.STAR3_DIMS}
+    fact = {"fk_" + name[2:]: datagen.uniform_int_torch(datagen.DEFAULT_SEED, 611 + j, n, 0, rows, torch.int32,
+                                                         device="cuda")
+            for j, (name, rows) in enumerate(datagen.STAR3_DIMS)}
+    fact["revenue"] = datagen.uniform_int_torch(datagen.DEFAULT_SEED, 619, n, 100, 10_000_000, torch.int64,
+                                                device="cuda")
+    ctx.register_table("fact", fact)
+    _register_host(ctx, dims)
+    host = {"fact": {c: v.cpu().numpy() for c, v in fact.items()}, **dims}
+    plan = workloads.star3_plan()
+    w = _oracle(plan, host)
+    assert len(w[0]) == 5 * 5 * 6
+    for kind, kw in (("perfect", dict(agg="global", ht="perfect", pred="compacted", items_per_thread=1, block=512)),
+                     ("perfect", dict(agg="local", ht="perfect", pred="branch", items_per_thread=1, block=512)),
+                     ("linear", dict(agg="global", ht="linear", pred="predicated", items_per_thread=1)),
+                     ("cuckoo", dict(agg="local", ht="linear", pred="compacted", items_per_thread=1, block=256))):
+        assert_same(ctx.query(plan, pv.variant(**kw), pv.ht_variant(kind)), w, ctxmsg=f"{kind} {kw}")

@@ -716,3 +716,57 @@ def test_cluster_tables_unsupported_cases(ctx):
     with pytest.raises(pv.PVError) as e:
         ctx.query(plan, pv.variant(agg="cluster", ht="perfect", items_per_thread=1))
     assert e.value.status == -2
+
+
+# ---------------------------------------------------------------- three-part group keys
+@pytest.mark.parametrize("n,spans,lows", [(0, (16, 64, 7), (0, 0, 1992)), (5, (16, 64, 7), (0, 0, 1992)),
+                                          (100_003, (16, 64, 7), (0, 0, 1992)), (60_001, (3, 1, 2), (-7, 5, 0))])
+def test_three_part_keys_all_variants(ctx, n, spans, lows):
+    k3 = {"k3": datagen.table_keys3(n, spans, lows, seed=n + 3)}
+    register(ctx, k3)
+    plan = workloads.keys3_plan()
+    _grouped_all_variants(ctx, plan, k3, step=3, min_ran=20)
+    _cluster(ctx, plan, k3, step=3, min_ran=8)
+    for kw in (dict(warp_agg=1, agg="global", ht="perfect", items_per_thread=1),
+               dict(warp_agg=1, agg="global", ht="linear", items_per_thread=1)):
+        assert_same(ctx.query(plan, pv.variant(**kw)), want(plan, k3), ctxmsg=str(kw))
+
+
+def test_three_part_keys_wide_domain(ctx):
+    # 5000^3 = 1.25e11 codes: past 2^32 (64-bit codes in the hash tables),
+    # below the 2^40 bound; a perfect array (at most 2^28 slots) is refused
+    k3 = {"k3": datagen.table_keys3(80_001, (5000, 5000, 5000), (-2500, 0, 7), seed=5)}
+    register(ctx, k3)
+    plan = workloads.keys3_plan()
+    _grouped_all_variants(ctx, plan, k3, step=5, min_ran=8)
+    with pytest.raises(pv.PVError) as e:
+        ctx.query(plan, pv.variant(agg="global", ht="perfect", items_per_thread=1))
+    assert e.value.status == -2
+    # 20001^3 > 2^40 codes: no table kind takes the key
+    big = {"k3": {"a": np.array([0, 20_000], np.int32), "b": np.array([0, 20_000], np.int32),
+                  "c": np.array([0, 20_000], np.int32), "val": np.array([1, 2], np.int64)}}
+    register(ctx, big)
+    for kw in (dict(ht="linear"), dict(ht="cuckoo", exec="multi"), dict(ht="perfect", agg="global")):
+        with pytest.raises(pv.PVError) as e:
+            ctx.query(plan, pv.variant(items_per_thread=1, **kw))
+        assert e.value.status == -2, kw
+
+
+@pytest.mark.parametrize("build_kind", ["linear", "cuckoo", "perfect"])
+def test_star3_groups_on_three_payloads(ctx, build_kind):
+    s = datagen.star3_schema(150_007, seed=37)
+    register(ctx, s)
+    htv = pv.ht_variant(build_kind)
+    for plan in (workloads.star3_plan(), workloads.star3_plan(regions=(0, 4), years=(1992, 1998))):
+        w = want(plan, s)
+        assert len(w[0]) > 100
+        ran = 0
+        for kw in GROUP_VARIANTS[::5]:
+            got = run_or_skip(ctx, plan, pv.variant(**kw), htv)
+            if got is None:
+                continue
+            ran += 1
+            assert_same(got, w, ctxmsg=f"{build_kind} {kw}")
+        assert ran >= 10
+        _compacted(ctx, plan, s, htv, step=5, min_ran=10)
+        _cluster(ctx, plan, s, htv, step=4, min_ran=6)

@@ -79,6 +79,23 @@ def test_grouped_lattice_closed_form(g, n):
     assert _as_lists(res) == [ks, sums, j]
 
 
+@pytest.mark.parametrize("spans,m", [((3, 4, 5), 7), ((2, 1, 9), 3), ((5, 5, 1), 1)])
+def test_three_part_key_lattice_closed_form(spans, m):
+    # Row i = q + P*j (P = A*B*C, j < m) has parts (q mod A, (q div A) mod B,
+    # q div AB) offset by (-1, 10, 1992) and val = i: every one of the P groups
+    # holds m rows, with SUM(val) = m*q + P*m*(m-1)/2.
+    A, B, C = spans
+    P = A * B * C
+    i = np.arange(P * m)
+    q = i % P
+    k3 = {"a": (q % A - 1).astype(np.int32), "b": ((q // A) % B + 10).astype(np.int32),
+          "c": (q // (A * B) + 1992).astype(np.int32), "val": i.astype(np.int64)}
+    got = sorted(zip(*_as_lists(oracle.run(workloads.keys3_plan(), {"k3": k3}))))
+    want = sorted((qq % A - 1, (qq // A) % B + 10, qq // (A * B) + 1992, m * qq + P * m * (m - 1) // 2, m)
+                  for qq in range(P))
+    assert got == want
+
+
 def test_product_aggregates_closed_form():
     # disc = i mod 11, tax = i mod 9 (every (disc, tax) pair m times over
     # 99 m rows, by the Chinese remainder theorem), price = P, qty = 2;
@@ -165,7 +182,8 @@ def _random_case(rng: random.Random):
     if rng.random() < 0.25:
         plan["project"] = rng.sample(refs, rng.randint(1, 3))
     else:
-        plan["group_by"] = rng.sample([r for r in refs if r != "v"], rng.randint(0, 2))
+        keyable = [r for r in refs if r != "v"]
+        plan["group_by"] = rng.sample(keyable, rng.randint(0, min(3, len(keyable))))
         aggs = []
         for _ in range(rng.randint(1, 4)):
             f = rng.choice(["sum", "count", "min", "max"])
