@@ -63,8 +63,8 @@ TUNED = {
     "filter_project": dict(exec="single", pred="branch", access="grid", items_per_thread=4, block=128),
     "keyval": dict(agg="local", ht="perfect", pred="branch", access="grid", items_per_thread=1, block=512),
     "star": dict(agg="global", ht="perfect", pred="compacted", access="grid", items_per_thread=1, block=512),
-    "keys3": dict(agg="cluster", ht="perfect", pred="branch", access="grid", items_per_thread=1, block=512,
-                  warp_agg=1),
+    "keys3": dict(agg="local", ht="perfect", pred="branch", access="grid", items_per_thread=1, block=1024,
+                  prefetch=1),
     "star3": dict(agg="global", ht="perfect", pred="compacted", access="grid", items_per_thread=1, block=512),
 }
 

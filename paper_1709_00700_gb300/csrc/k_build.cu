@@ -196,9 +196,11 @@ pv_status build_table(const BuildEnv& env, const BuildInput& in, const pv_ht_var
   }
   const int max_ev = var.max_evictions > 0 ? var.max_evictions : 32 * std::max(1, h.log2cap);
   out.n_payload = in.n_payload;
-  // [slots | 16-byte stats | presence bits (perfect arrays without payload)]
+  // [slots | 16-byte stats | presence bits (perfect arrays without payload or past 64 KB of slots: the
+  // bits stay in L1 where the slots would not, and only hits read a slot)]
   const size_t stats_off = (bytes + 15) & ~size_t(15);
-  const bool with_bits = var.kind == PV_HT_PERFECT && in.n_payload == 0;
+  const bool with_bits = var.kind == PV_HT_PERFECT && (in.n_payload == 0 || h.cap * 8 > (64 << 10));
+  h.payload = in.n_payload > 0 ? 1 : 0;
   const size_t bits_bytes = with_bits ? static_cast<size_t>((h.cap + 31) / 32) * 4 : 0;
   out.mem = env.alloc(stats_off + 16 + bits_bytes + 64, env.user);
   if (!out.mem) {

@@ -24,7 +24,8 @@
 namespace pv {
 
 constexpr int kLocalProbe = 16;          // probe-length bound in a local table
-constexpr size_t kLocalBytes = 96 << 10; // shared memory of a CTA-local table
+constexpr size_t kLocalBytes = 96 << 10; // shared memory of a CTA-local hash table
+constexpr size_t kLocalPerfectBytes = 192 << 10;  // of a CTA-local perfect array (one CTA per SM past 113 KB)
 constexpr size_t kClusterBytes = 192 << 10;  // shared memory of one CTA's part of a cluster table
 
 // Whether every group-key part is a 32-bit source.
@@ -975,7 +976,7 @@ static pv_status launch_group(const LaunchCfg& c, const KParams& kp, const Group
       s = run_group<SH, UMASK, SinkThreadPerfect>(c, kp, gd, g, smem);
     } else {
       const size_t smem = static_cast<size_t>(g.cap) * slot_bytes;
-      if (smem > kLocalBytes) return PV_ERR_UNSUPPORTED;
+      if (smem > kLocalPerfectBytes) return PV_ERR_UNSUPPORTED;
       s = run_group<SH, UMASK, SinkLocalPerfect>(c, kp, gd, g, smem);
     }
     if (s != PV_OK) return s;

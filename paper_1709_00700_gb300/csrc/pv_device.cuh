@@ -32,12 +32,14 @@ constexpr uint32_t kEmpty32 = 0xFFFFFFFFu;
 // Perfect: slot (key - kmin) holds (payload << 32) | 1, 0 when empty.
 struct DevHT {
   uint64_t* slots;
-  const uint32_t* bits;  // perfect array without payload: presence bit per slot (probes read these), else null
+  const uint32_t* bits;  // perfect array without payload, or past 64 KB of slots: presence bit per
+                         // slot (probes test it first, then read the slot of a hit for its payload)
   int32_t kind;      // pv_ht_kind
   int32_t hash;      // pv_hash_fn
   int32_t log2cap;
   int32_t k;         // cuckoo functions
   int32_t narrow;    // perfect: kmin >= INT32_MIN and kmin + cap <= 2^31, so 32-bit keys index in 32 bits
+  int32_t payload;   // slots carry a payload
   int64_t cap;       // slots (power of two for linear/cuckoo; domain size for perfect)
   int64_t kmin;      // perfect: smallest key
   uint64_t seed[4];  // per-function hash seeds
@@ -308,8 +310,10 @@ __device__ __forceinline__ bool probe_key(const DevHT& h, int64_t key, int32_t& 
     const int64_t i = key - h.kmin;
     if (static_cast<uint64_t>(i) >= static_cast<uint64_t>(h.cap)) return false;
     if (h.bits != nullptr) {  // 1 bit per key instead of 8 bytes: small enough to stay in L1
-      pay = 0;
-      return (__ldg(h.bits + (i >> 5)) >> (i & 31)) & 1u;
+      const bool hit = (__ldg(h.bits + (i >> 5)) >> (i & 31)) & 1u;
+      pay = hit && h.payload ? static_cast<int32_t>(__ldg(reinterpret_cast<const unsigned long long*>(h.slots) + i) >> 32)
+                             : 0;
+      return hit;
     }
     const uint64_t s = __ldg(reinterpret_cast<const unsigned long long*>(h.slots) + i);
     pay = static_cast<int32_t>(s >> 32);
@@ -343,7 +347,7 @@ __device__ __forceinline__ bool probe_key(const DevHT& h, int64_t key, int32_t& 
 }
 
 // HASH_PROBE of the 4 rows of an item; returns the mask with the misses
-// cleared and binds each hit's payload (0 for a miss).  Perfect tables
+// cleared and binds the payload of each hit in mask (0 otherwise).  Perfect tables
 // (the kind is the same for every lane) probe all 4 rows without branches:
 // 4 independent read-only loads, a dead row of a live item costing one cache
 // hit.  Hashed tables probe the live rows (every row when all_rows) one at a
@@ -359,14 +363,22 @@ __device__ __forceinline__ uint32_t probe_item(const DevHT& h, const T (&fk)[4],
       if (h.narrow) {
         const uint32_t k0 = static_cast<uint32_t>(h.kmin), cap = static_cast<uint32_t>(h.cap);
         if (h.bits != nullptr) {
+          uint32_t ic[4];
 #pragma unroll
           for (int r = 0; r < 4; ++r) {
             const uint32_t i = static_cast<uint32_t>(static_cast<int32_t>(fk[r])) - k0;
             const bool in = i < cap;
-            const uint32_t ic = in ? i : 0u;
-            const uint32_t w = __ldg(h.bits + (ic >> 5));
-            hit |= static_cast<uint32_t>(in & ((w >> (ic & 31u)) & 1u)) << r;
+            ic[r] = in ? i : 0u;
+            const uint32_t w = __ldg(h.bits + (ic[r] >> 5));
+            hit |= static_cast<uint32_t>(in & ((w >> (ic[r] & 31u)) & 1u)) << r;
             pay[r] = 0;
+          }
+          if (h.payload) {  // payload slots of the surviving hits only
+            const uint32_t need = mask & hit;
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+              if ((need >> r) & 1u)
+                pay[r] = static_cast<int32_t>(__ldg(reinterpret_cast<const unsigned long long*>(h.slots) + ic[r]) >> 32);
           }
         } else {
 #pragma unroll
@@ -383,14 +395,22 @@ __device__ __forceinline__ uint32_t probe_item(const DevHT& h, const T (&fk)[4],
       }
     }
     if (h.bits != nullptr) {
+      uint64_t ic[4];
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         const uint64_t i = static_cast<uint64_t>(static_cast<int64_t>(fk[r]) - h.kmin);
         const bool in = i < static_cast<uint64_t>(h.cap);
-        const uint64_t ic = in ? i : 0;
-        const uint32_t w = __ldg(h.bits + (ic >> 5));
-        hit |= static_cast<uint32_t>(in && ((w >> (ic & 31)) & 1u)) << r;
+        ic[r] = in ? i : 0;
+        const uint32_t w = __ldg(h.bits + (ic[r] >> 5));
+        hit |= static_cast<uint32_t>(in && ((w >> (ic[r] & 31)) & 1u)) << r;
         pay[r] = 0;
+      }
+      if (h.payload) {
+        const uint32_t need = mask & hit;
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          if ((need >> r) & 1u)
+            pay[r] = static_cast<int32_t>(__ldg(reinterpret_cast<const unsigned long long*>(h.slots) + ic[r]) >> 32);
       }
     } else {
 #pragma unroll

@@ -58,9 +58,12 @@ GRIDS = {
                [dict(s, pred="compacted", items_per_thread=1, block=256, prefetch=0)
                 for s in [dict(agg="local", ht="perfect"), dict(agg="global", ht="perfect"),
                           dict(agg="local", ht="linear"), dict(agg="global", ht="linear")]] +
-               # perfect array in the distributed shared memory of a cluster of 8 CTAs
+               # perfect array in the distributed shared memory of a cluster of 2 to 16 CTAs
                [dict(agg="cluster", ht="perfect", pred="branch", items_per_thread=1, block=512, prefetch=0,
-                     warp_agg=w) for w in (0, 1)],
+                     warp_agg=w) for w in (0, 1)] +
+               # CTA-local perfect arrays past 113 KB leave room for one CTA per SM: 1024 threads keep it busy
+               [dict(agg="local", ht="perfect", pred="branch", items_per_thread=1, block=1024, prefetch=f)
+                for f in (0, 1)],
     "star": [dict(s, build=bk, pred=p, items_per_thread=1, block=512, prefetch=f)
              for bk, s, p, f in itertools.product(
                  ["perfect", "linear", "cuckoo"],

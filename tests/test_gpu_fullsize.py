@@ -147,7 +147,8 @@ def test_three_part_keys_60m_rows(ctx):
     plan = workloads.keys3_plan()
     w = _oracle(plan, host)
     assert len(w[0]) == 16 * 64 * 7 and int(w[4].sum()) == n
-    for kw in (dict(agg="cluster", ht="perfect", pred="branch", items_per_thread=1, block=512, warp_agg=1),
+    for kw in (dict(agg="local", ht="perfect", pred="branch", items_per_thread=1, block=1024, prefetch=1),  # bench
+               dict(agg="cluster", ht="perfect", pred="branch", items_per_thread=1, block=512, warp_agg=1),
                dict(agg="global", ht="perfect", pred="predicated", items_per_thread=1, block=256),
                dict(agg="global", ht="linear", pred="predicated", items_per_thread=1, warp_agg=1),
                dict(agg="local", ht="cuckoo", exec="multi", items_per_thread=1)):

@@ -728,7 +728,8 @@ def test_three_part_keys_all_variants(ctx, n, spans, lows):
     _grouped_all_variants(ctx, plan, k3, step=3, min_ran=20)
     _cluster(ctx, plan, k3, step=3, min_ran=8)
     for kw in (dict(warp_agg=1, agg="global", ht="perfect", items_per_thread=1),
-               dict(warp_agg=1, agg="global", ht="linear", items_per_thread=1)):
+               dict(warp_agg=1, agg="global", ht="linear", items_per_thread=1),
+               dict(agg="local", ht="perfect", items_per_thread=1, block=1024, prefetch=1)):
         assert_same(ctx.query(plan, pv.variant(**kw)), want(plan, k3), ctxmsg=str(kw))
 
 
