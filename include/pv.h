@@ -68,8 +68,10 @@ typedef int32_t pv_graph; /* captured-graph handle */
 #define PV_MAX_PROJ 4
 #define PV_MAX_PAYLOAD 1
 
-/* FILTER comparison (Table 1): column op constant, or lo <= column <= hi. */
-typedef enum { PV_LT = 0, PV_LE = 1, PV_GT = 2, PV_GE = 3, PV_EQ = 4, PV_BETWEEN = 5 } pv_cmp;
+/* FILTER comparison (Table 1): column op constant, or lo <= column <= hi.
+ * PV_PREFIX (string starts with a constant) is for pv_dict_range only; a
+ * pv_pred never carries it. */
+typedef enum { PV_LT = 0, PV_LE = 1, PV_GT = 2, PV_GE = 3, PV_EQ = 4, PV_BETWEEN = 5, PV_PREFIX = 6 } pv_cmp;
 /* Distributive aggregate functions (Section 7.5). */
 typedef enum { PV_SUM = 0, PV_COUNT = 1, PV_MIN = 2, PV_MAX = 3 } pv_func;
 /* ARITHMETIC term (Table 1): x, x + c or c - x; an aggregate's value is the
@@ -287,6 +289,33 @@ pv_status pv_atomic_peak(pv_ctx* ctx, int64_t slots, int32_t words, int64_t n_up
 /* Enqueues one kernel that busy-waits for `ns` nanoseconds of GPU clock
  * (bounded; for exercising the pv_sync watchdog). */
 pv_status pv_debug_spin(pv_ctx* ctx, int64_t ns);
+
+/* ---- dictionary-coded strings ------------------------------------------- */
+
+/* String predicates of FILTER (Table 1; Section 9.2.1 names the missing LIKE
+ * operator as the reason some SSB and TPC-H queries were left out).  A string
+ * column is an int32 column of codes into a dictionary: dict[0..n_entries)
+ * are distinct NUL-terminated strings in strictly ascending byte order
+ * (strcmp), and a row's code is the rank of its string.  Codes order like the
+ * strings, so these host-only calls (no ctx, no device work) turn a string
+ * predicate into a predicate on the codes.  The caller owns every buffer.
+ * Errors: PV_ERR_INVALID_ARG for null pointers, n_entries outside 0..2^31-1,
+ * a dictionary that is not strictly ascending, or a bad op. */
+
+/* Inclusive code range [*lo, *hi] of the rows whose string s satisfies
+ * s op s0 (PV_LT, PV_LE, PV_GT, PV_GE, PV_EQ), s0 <= s <= s1 (PV_BETWEEN), or
+ * s starts with s0 (PV_PREFIX).  The constants need not be in the dictionary.
+ * An empty range is returned as *lo = 1, *hi = 0.  s1 is read for
+ * PV_BETWEEN only. */
+pv_status pv_dict_range(const char* const* dict, int64_t n_entries, int32_t op, const char* s0, const char* s1,
+                        int64_t* lo, int64_t* hi);
+/* Codes of the dictionary strings that match the SQL LIKE pattern ('%' any
+ * run of bytes, '_' one byte, no escape character), ascending: the first
+ * min(count, capacity) go to codes[], the count to *n_match.  A set that is
+ * not one range is applied as a semi-join: a build pipeline over these codes
+ * and a HASH_PROBE of the code column. */
+pv_status pv_dict_match(const char* const* dict, int64_t n_entries, const char* pattern, int32_t* codes,
+                        int64_t capacity, int64_t* n_match);
 
 /* ---- cost model --------------------------------------------------------- */
 

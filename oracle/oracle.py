@@ -16,7 +16,9 @@ Neutral plan (the query written as the pipeline programs of Table 2):
       "aggs":    [agg...],
       "project": [ref...],                   # PROJECT (mutually exclusive with aggs)
     }
-    pred = (col, op, c) with op in lt/le/gt/ge/eq, or (col, "between", lo, hi)
+    pred = (col, op, c) with op in lt/le/gt/ge/eq, or (col, "between", lo, hi);
+           on a column of strings (a numpy str or bytes array) also
+           (col, "prefix", s), (col, "like", pattern), (col, "in", [s...])
     ref  = "col" (fact column) or ("payload", probe_index, payload_index)
     agg  = ("count",) or (func, [term...]) with func in sum/min/max and the
            value the product of its terms (ARITHMETIC)
@@ -26,6 +28,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import re
 import subprocess
 
 import numpy as np
@@ -165,6 +168,90 @@ def encode(plan: dict, tables: dict):
     return np.array(w, dtype=np.int64), enc
 
 
+# String predicates (FILTER of Table 1 on text attributes; the SQL LIKE of
+# Section 9.2.1).  Each is evaluated here on the strings themselves, row by
+# row, into a 0/1 int32 column that the plan then filters with "eq 1".
+# Strings compare by code point (str) or byte (bytes).
+def _like_regex(pattern):
+    """SQL LIKE as a regular expression: '%' any run, '_' one character."""
+    text = pattern.decode("latin-1") if isinstance(pattern, bytes) else pattern
+    body = "".join(".*" if ch == "%" else "." if ch == "_" else re.escape(ch) for ch in text)
+    return re.compile(body, re.DOTALL)
+
+
+def _string_test(p, as_bytes: bool):
+    conv = (lambda x: x.encode() if isinstance(x, str) else x) if as_bytes else \
+           (lambda x: x.decode() if isinstance(x, bytes) else x)
+    op = p[1]
+    if op == "like":
+        rx = _like_regex(p[2])
+        if as_bytes:
+            return lambda v: rx.fullmatch(v.decode("latin-1")) is not None
+        return lambda v: rx.fullmatch(v) is not None
+    if op == "in":
+        members = {conv(x) for x in p[2]}
+        return lambda v: v in members
+    c0 = conv(p[2])
+    if op == "lt":
+        return lambda v: v < c0
+    if op == "le":
+        return lambda v: v <= c0
+    if op == "gt":
+        return lambda v: v > c0
+    if op == "ge":
+        return lambda v: v >= c0
+    if op == "eq":
+        return lambda v: v == c0
+    if op == "between":
+        c1 = conv(p[3])
+        return lambda v: c0 <= v <= c1
+    if op == "prefix":
+        return lambda v: v.startswith(c0)
+    raise OracleError(-1, f"bad string predicate {p}")
+
+
+def _is_text(a) -> bool:
+    """Columns of strings: numpy str / bytes arrays, or object arrays (which
+    hold nothing but text in a table)."""
+    return np.asarray(a).dtype.kind in ("U", "S", "O")
+
+
+def resolve_string_filters(plan: dict, tables: dict):
+    """Returns (plan, tables) in which every predicate on a column of strings
+    is replaced by "eq 1" on a 0/1 int32 column holding its value per row."""
+    if not any(_is_text(c) for t in tables.values() for c in t.values()):
+        return plan, tables
+    plan = dict(plan)
+    tables = {t: dict(cols) for t, cols in tables.items()}
+    made = [0]
+
+    def rewrite(table, preds):
+        out = []
+        for p in preds:
+            col = tables[table].get(p[0])
+            if col is None or not _is_text(col):
+                out.append(p)
+                continue
+            a = np.asarray(col)
+            test = _string_test(p, a.dtype.kind == "S" or (a.dtype.kind == "O" and len(a) > 0 and isinstance(a[0], bytes)))
+            seen = {}
+            flags = np.empty(len(a), dtype=np.int32)
+            for i, v in enumerate(a.tolist()):
+                f = seen.get(v)
+                if f is None:
+                    f = seen[v] = 1 if test(v) else 0
+                flags[i] = f
+            name = f"__text{made[0]}"
+            made[0] += 1
+            tables[table][name] = flags
+            out.append([name, "eq", 1])
+        return out
+
+    plan["builds"] = [dict(b, filters=rewrite(b["table"], b.get("filters", []))) for b in plan.get("builds", [])]
+    plan["filters"] = rewrite(plan["fact"], plan.get("filters", []))
+    return plan, tables
+
+
 def fact_rows(plan: dict, tables: dict) -> int:
     fact = tables[plan["fact"]]
     return len(next(iter(fact.values())))
@@ -177,6 +264,7 @@ def run(plan: dict, tables: dict, nthreads: int = 1) -> dict:
     columns then aggregate columns, ascending by key), or "project" (projected
     columns in input order)."""
     lib = _load()
+    plan, tables = resolve_string_filters(plan, tables)
     words, enc = encode(plan, tables)
     n = len(enc.cols)
     ptrs = (ctypes.c_void_p * max(n, 1))(*[a.ctypes.data for a in enc.cols])

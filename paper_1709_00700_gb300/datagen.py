@@ -239,6 +239,32 @@ STAR3_DIMS = (("d_cust", 30_000), ("d_supp", 2_000), ("d_date", 2_556))
 STAR3_YEAR0 = 1992
 
 
+# Dictionary-coded text attributes shaped like SSB's: part categories
+# "MFGR#mk" and brands "MFGR#mkjj" (40 per category), and region names.  Each
+# dictionary is sorted, so an attribute's int32 code is its string's rank.
+SSB_REGIONS = ("AFRICA", "AMERICA", "ASIA", "EUROPE", "MIDDLE EAST")
+
+
+def part_categories() -> list:
+    return [f"MFGR#{m}{k}" for m in range(1, 6) for k in range(1, 6)]
+
+
+def part_brands() -> list:
+    return [f"MFGR#{m}{k}{j:02d}" for m in range(1, 6) for k in range(1, 6) for j in range(1, 41)]
+
+
+def table_parts(n: int, seed: int = DEFAULT_SEED) -> dict:
+    """category and brand int32 codes (a brand belongs to its category), price int64 uniform [100, 1e7)."""
+    cat = uniform_int(seed, 701, n, 0, 25, np.int32)
+    brand = (cat.astype(np.int64) * 40 + uniform_int(seed, 702, n, 0, 40, np.int64)).astype(np.int32)
+    return {"category": cat, "brand": brand, "price": uniform_int(seed, 703, n, 100, 10_000_000, np.int64)}
+
+
+def as_text(codes, dictionary) -> np.ndarray:
+    """The strings of a dictionary-coded column."""
+    return np.asarray(dictionary)[np.asarray(codes)]
+
+
 def star3_dimension(name: str, seed: int = DEFAULT_SEED) -> dict:
     idx = [d[0] for d in STAR3_DIMS].index(name)
     rows = STAR3_DIMS[idx][1]

@@ -127,6 +127,10 @@ _SIGS = {
                                           _P(ctypes.c_int64), ctypes.c_int32]),
     "pv_atomic_peak": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64,
                                         ctypes.POINTER(ctypes.c_float)]),
+    "pv_dict_range": (ctypes.c_int32, [_P(ctypes.c_char_p), ctypes.c_int64, ctypes.c_int32, ctypes.c_char_p,
+                                       ctypes.c_char_p, _P(ctypes.c_int64), _P(ctypes.c_int64)]),
+    "pv_dict_match": (ctypes.c_int32, [_P(ctypes.c_char_p), ctypes.c_int64, ctypes.c_char_p, _P(ctypes.c_int32),
+                                       ctypes.c_int64, _P(ctypes.c_int64)]),
     "pv_filter_project_noalloc": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                                    ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
@@ -187,6 +191,122 @@ def _type_of(t) -> int:
     return m[t.dtype]
 
 
+# ---- dictionary-coded strings ------------------------------------------------
+STR_OPS = {"lt": 0, "le": 1, "gt": 2, "ge": 3, "eq": 4, "between": 5, "prefix": 6}
+
+
+class Dictionary:
+    """The sorted distinct strings of a dictionary-coded column (a row's code is
+    its string's rank), and the host calls that turn string predicates into code
+    ranges or code sets (pv_dict_range, pv_dict_match)."""
+
+    def __init__(self, strings):
+        self.strings = [x.encode() if isinstance(x, str) else bytes(x) for x in strings]
+        self._arr = (ctypes.c_char_p * max(len(self.strings), 1))(*self.strings)
+        self.lib = load()
+
+    def __len__(self):
+        return len(self.strings)
+
+    def _check(self, st):
+        if st != PV_OK:
+            raise PVError(st, "string dictionary: not strictly ascending, or a bad predicate")
+
+    def range(self, op: str, s0, s1=None) -> tuple:
+        """Inclusive code range of `column op s0` (or s0 <= column <= s1); (1, 0) if empty."""
+        lo, hi = ctypes.c_int64(), ctypes.c_int64()
+        b0 = s0.encode() if isinstance(s0, str) else bytes(s0)
+        b1 = None if s1 is None else (s1.encode() if isinstance(s1, str) else bytes(s1))
+        self._check(self.lib.pv_dict_range(self._arr, len(self.strings), STR_OPS[op], b0, b1,
+                                           ctypes.byref(lo), ctypes.byref(hi)))
+        return lo.value, hi.value
+
+    def match(self, pattern) -> np.ndarray:
+        """Ascending codes of the strings matching a SQL LIKE pattern."""
+        pat = pattern.encode() if isinstance(pattern, str) else bytes(pattern)
+        n = ctypes.c_int64()
+        self._check(self.lib.pv_dict_match(self._arr, len(self.strings), pat, None, 0, ctypes.byref(n)))
+        out = np.empty(n.value, dtype=np.int32)
+        self._check(self.lib.pv_dict_match(self._arr, len(self.strings), pat,
+                                           out.ctypes.data_as(_P(ctypes.c_int32)), n.value, ctypes.byref(n)))
+        return out
+
+    def codes_of(self, strings) -> np.ndarray:
+        """Ascending codes of those of `strings` that are in the dictionary."""
+        got = []
+        for x in strings:
+            lo, hi = self.range("eq", x)
+            if lo <= hi:
+                got.append(lo)
+        return np.unique(np.array(got, dtype=np.int32))
+
+    def decode(self, codes) -> list:
+        return [self.strings[int(c)].decode() for c in codes]
+
+
+def _is_string_pred(p) -> bool:
+    return any(isinstance(c, (str, bytes, list, tuple)) for c in p[2:])
+
+
+def _string_pred_codes(d: Dictionary, p):
+    """('range', lo, hi) or ('set', codes) of a string predicate."""
+    op = p[1]
+    if op == "between":
+        return ("range",) + d.range("between", p[2], p[3])
+    if op in STR_OPS:
+        return ("range",) + d.range(op, p[2])
+    if op == "like":
+        codes = d.match(p[2])
+    elif op == "in":
+        codes = d.codes_of(p[2])
+    else:
+        raise PVError(-1, f"bad string predicate {p}")
+    if len(codes) == 0:
+        return ("range", 1, 0)
+    if int(codes[-1]) - int(codes[0]) + 1 == len(codes):
+        return ("range", int(codes[0]), int(codes[-1]))
+    return ("set", codes)
+
+
+def resolve_strings(plan: dict, dicts: dict):
+    """Rewrites the string predicates of a plan ([col, op, "text"...] on a column
+    registered with a dictionary; dicts maps (table, column) to its Dictionary)
+    into predicates on the codes.  Comparisons, BETWEEN and "prefix", and "like" /
+    "in" whose codes form one range, become one code range.  Other "like" / "in"
+    predicates on the fact table become a semi-join: a build pipeline over the
+    matching codes (no payload) and a probe of the column, appended after the
+    plan's probes.  Returns (plan, [(set table name, int32 codes)])."""
+    import copy
+    plan = copy.deepcopy(plan)
+    sets = []
+    for b in plan.get("builds", []):
+        out = []
+        for p in b.get("filters", []):
+            if (b["table"], p[0]) in dicts and _is_string_pred(p):
+                r = _string_pred_codes(dicts[(b["table"], p[0])], p)
+                if r[0] == "set":
+                    raise PVError(-2, f"build filter {p}: codes that are not one range")
+                p = [p[0], "between", r[1], r[2]]
+            out.append(p)
+        b["filters"] = out
+    fact = plan["fact"]
+    out = []
+    for p in plan.get("filters", []):
+        if (fact, p[0]) in dicts and _is_string_pred(p):
+            r = _string_pred_codes(dicts[(fact, p[0])], p)
+            if r[0] == "range":
+                out.append([p[0], "between", r[1], r[2]])
+                continue
+            name = f"__codes{len(sets)}"
+            sets.append((name, r[1]))
+            plan.setdefault("builds", []).append({"table": name, "key": "code", "filters": [], "payload": []})
+            plan.setdefault("probes", []).append({"build": len(plan["builds"]) - 1, "fk": p[0]})
+            continue
+        out.append(p)
+    plan["filters"] = out
+    return plan, sets
+
+
 class Context:
     """One pv_ctx on a dedicated CUDA stream, allocating through torch."""
 
@@ -217,6 +337,7 @@ class Context:
         self.cols = {}      # (table, col) -> handle
         self.keep = {}      # (table, col) -> tensor (borrowed by libpv)
         self.tables = {}    # build key -> ht handle
+        self.dicts = {}     # (table, col) -> Dictionary of a dictionary-coded column
 
     # -- plumbing -------------------------------------------------------------
     def _check(self, st: int, ctx="self"):
@@ -264,9 +385,14 @@ class Context:
         return [buf[i] for i in range(min(n.value, 64))]
 
     # -- columns ----------------------------------------------------------------
-    def register_table(self, table: str, cols: dict):
-        """Registers device tensors (1-D, contiguous) as borrowed columns."""
+    def register_table(self, table: str, cols: dict, dicts: dict | None = None):
+        """Registers device tensors (1-D, contiguous) as borrowed columns.  dicts
+        maps a column holding int32 codes to its dictionary (sorted distinct
+        strings, or a Dictionary): string predicates on it are then resolved by
+        query()."""
         torch = self.torch
+        for name, d in (dicts or {}).items():
+            self.dicts[(table, name)] = d if isinstance(d, Dictionary) else Dictionary(d)
         self.stream.wait_stream(torch.cuda.current_stream(self.device))
         for name, t in cols.items():
             if not isinstance(t, torch.Tensor):
@@ -286,6 +412,9 @@ class Context:
 
     # -- builds -----------------------------------------------------------------
     def _pred(self, table, p) -> pv_pred:
+        if _is_string_pred(p) or p[1] not in OPS:
+            raise PVError(-1, f"predicate {p} on {table}: string predicates are resolved by query() "
+                              "(or resolve_strings) on columns registered with a dictionary")
         c1 = int(p[3]) if p[1] == "between" else 0
         return pv_pred(self.cols[(table, p[0])], OPS[p[1]], int(p[2]), c1)
 
@@ -379,7 +508,11 @@ class Context:
 
     def query(self, plan: dict, var: pv_variant, htv: pv_ht_variant | None = None, keep: bool = False):
         """Builds, runs and fetches a whole plan; returns int64 result columns
-        (grouped results sorted by key, projections as produced)."""
+        (grouped results sorted by key, projections as produced).  String
+        predicates on dictionary-coded columns are resolved first."""
+        plan, sets = resolve_strings(plan, self.dicts)
+        for name, codes in sets:
+            self.register_table(name, {"code": codes})
         hts = self.build_all(plan, htv or ht_variant())
         res = self.run(plan, var, hts)
         cols = [c.astype(np.int64) for c in self.fetch(res)]

@@ -97,3 +97,11 @@ def star3_plan(regions=STAR3_REGIONS, years=STAR3_YEARS) -> dict:
             "probes": [{"build": 0, "fk": "fk_cust"}, {"build": 1, "fk": "fk_supp"}, {"build": 2, "fk": "fk_date"}],
             "group_by": [["payload", 0, 0], ["payload", 1, 0], ["payload", 2, 0]],
             "aggs": [["sum", [["x", "revenue"]]]]}
+
+
+# Filter/aggregate on dictionary-coded part attributes, shaped like the part
+# selection of SSB Q2.2: category = c AND brand BETWEEN b0 AND b1 ->
+# SUM(price), COUNT(*).  Other string predicates replace the two filters.
+def parts_text_plan(filters=(("category", "eq", "MFGR#12"), ("brand", "between", "MFGR#1221", "MFGR#1228"))) -> dict:
+    return {"fact": "parts", "filters": [list(f) for f in filters],
+            "aggs": [["sum", [["x", "price"]]], ["count"]]}

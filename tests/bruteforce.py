@@ -10,6 +10,8 @@ from __future__ import annotations
 
 import itertools
 
+import numpy as np
+
 M64 = 1 << 64
 
 
@@ -18,8 +20,35 @@ def wrap(v: int) -> int:
     return v - M64 if v >= (1 << 63) else v
 
 
-def _holds(v: int, p) -> bool:
+def _cell(v):
+    """A table cell: text stays text, numbers become Python integers."""
+    if isinstance(v, (str, bytes)):
+        return v
+    if isinstance(v, np.generic) and v.dtype.kind in ("U", "S"):
+        return v.item()
+    return int(v)
+
+
+def like(s, pattern) -> bool:
+    """SQL LIKE by recursion on the pattern: '%' matches nothing or one more
+    character, '_' one character, anything else itself."""
+    if not pattern:
+        return not s
+    if pattern[0] == "%":
+        return like(s, pattern[1:]) or (len(s) > 0 and like(s[1:], pattern))
+    if s and (pattern[0] == "_" or pattern[0] == s[0]):
+        return like(s[1:], pattern[1:])
+    return False
+
+
+def _holds(v, p) -> bool:
     op = p[1]
+    if op == "prefix":
+        return v[:len(p[2])] == p[2]
+    if op == "like":
+        return like(v, p[2])
+    if op == "in":
+        return any(v == x for x in p[2])
     if op == "lt":
         return v < p[2]
     if op == "le":
@@ -47,7 +76,7 @@ def evaluate(plan: dict, tables: dict) -> dict:
     for b in builds:
         t = tables[b["table"]]
         m = len(t[b["key"]])
-        rows = [r for r in range(m) if all(_holds(int(t[p[0]][r]), p) for p in b.get("filters", []))]
+        rows = [r for r in range(m) if all(_holds(_cell(t[p[0]][r]), p) for p in b.get("filters", []))]
         keys = [int(t[b["key"]][r]) for r in rows]
         if len(keys) != len(set(keys)):
             raise DuplicateBuildKey()
@@ -64,7 +93,7 @@ def evaluate(plan: dict, tables: dict) -> dict:
     matches = []  # (fact row, tuple of matched build rows per probe)
     for r in range(n):
         for combo in itertools.product(*[surviving[q["build"]] for q in probes]):
-            ok = all(_holds(int(fact[p[0]][r]), p) for p in plan.get("filters", []))
+            ok = all(_holds(_cell(fact[p[0]][r]), p) for p in plan.get("filters", []))
             for j, q in enumerate(probes):
                 b = builds[q["build"]]
                 ok = ok and int(fact[q["fk"]][r]) == int(tables[b["table"]][b["key"]][combo[j]])

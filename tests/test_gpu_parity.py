@@ -771,3 +771,68 @@ def test_star3_groups_on_three_payloads(ctx, build_kind):
         assert ran >= 10
         _compacted(ctx, plan, s, htv, step=5, min_ran=10)
         _cluster(ctx, plan, s, htv, step=4, min_ran=6)
+
+
+# ---------------------------------------------------------------- dictionary-coded strings
+def _register_parts(ctx, n, seed):
+    from tests.gpu_util import to_device
+    codes = datagen.table_parts(n, seed=seed)
+    cats, brands = datagen.part_categories(), datagen.part_brands()
+    ctx.register_table("parts", to_device({"parts": codes})["parts"], dicts={"category": cats, "brand": brands})
+    return {"parts": {"category": datagen.as_text(codes["category"], cats),
+                      "brand": datagen.as_text(codes["brand"], brands), "price": codes["price"]}}
+
+
+# one code range per column (the filter/aggregate shape)
+STRING_RANGE_FILTERS = [
+    (("category", "eq", "MFGR#12"), ("brand", "between", "MFGR#1221", "MFGR#1228")),
+    (("category", "ge", "MFGR#3"), ("brand", "prefix", "MFGR#3")),
+    (("category", "lt", "MFGR#2"), ("brand", "like", "MFGR#1%")),
+    (("category", "in", ["MFGR#21", "MFGR#22", "MFGR#23"]), ("brand", "gt", "MFGR#2150")),
+    (("category", "eq", "MFGR#99"), ("brand", "le", "MFGR#5540")),
+]
+
+
+@pytest.mark.parametrize("n", [0, 5, 100_003])
+def test_string_range_predicates(ctx, n):
+    text = _register_parts(ctx, n, seed=n + 7)
+    for filters in STRING_RANGE_FILTERS:
+        plan = workloads.parts_text_plan(filters)
+        w = want(plan, text)
+        ran = 0
+        for kw in SCAN_VARIANTS[::9]:
+            got = run_or_skip(ctx, plan, pv.variant(**kw))
+            if got is None:
+                continue
+            ran += 1
+            assert_same(got, w, ctxmsg=f"{filters} {kw}")
+        assert ran >= 3
+
+
+@pytest.mark.parametrize("kind", ["linear", "cuckoo", "perfect"])
+def test_string_like_and_in_as_semi_joins(ctx, kind):
+    text = _register_parts(ctx, 90_001, seed=17)
+    for f in (["brand", "like", "MFGR#_2_5"], ["brand", "like", "%9"],
+              ["brand", "in", ["MFGR#1101", "MFGR#3340", "MFGR#5540", "nope"]]):
+        plan = {"fact": "parts", "filters": [f], "aggs": [["count"]]}
+        w = want(plan, text)
+        assert int(w[0][0]) > 0
+        assert_same(ctx.query(plan, pv.variant(), pv.ht_variant(kind)), w, ctxmsg=f"{kind} {f}")
+
+
+def test_star3_region_filters_as_strings(ctx):
+    from tests.gpu_util import to_device
+    s = datagen.star3_schema(120_001, seed=39)
+    text = {t: dict(c) for t, c in s.items()}
+    for t, cols in to_device(s).items():
+        dicts = {"region": datagen.SSB_REGIONS} if t in ("d_cust", "d_supp") else None
+        ctx.register_table(t, cols, dicts=dicts)
+        if dicts:
+            text[t]["region"] = datagen.as_text(s[t]["region"], datagen.SSB_REGIONS)
+    for regions in (("ASIA", "ASIA"), ("AFRICA", "MIDDLE EAST")):
+        plan = workloads.star3_plan(regions=regions)
+        w = want(plan, text)
+        assert len(w[0]) > 100
+        for kind, kw in (("perfect", dict(agg="global", ht="perfect", pred="compacted", items_per_thread=1, block=512)),
+                         ("linear", dict(agg="local", ht="perfect", pred="branch", items_per_thread=1, block=512))):
+            assert_same(ctx.query(plan, pv.variant(**kw), pv.ht_variant(kind)), w, ctxmsg=f"{regions} {kind} {kw}")
