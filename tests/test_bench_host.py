@@ -24,7 +24,8 @@ def _brute_sector_bytes(tables, plan):
             ok = True
             for col, op, *c in b["filters"]:
                 v = int(dim[col][r])
-                ok &= {"lt": v < c[0], "le": v <= c[0], "ge": v >= c[0], "between": c[0] <= v <= c[-1]}[op]
+                ok &= {"lt": v < c[0], "le": v <= c[0], "ge": v >= c[0], "eq": v == c[0],
+                       "between": c[0] <= v <= c[-1]}[op]
             if ok:
                 passing.add(int(dim[b["key"]][r]))
         fk = fact[p["fk"]]
@@ -58,3 +59,13 @@ def test_star_sector_bytes_bounds():
     s = datagen.star_schema(100_000)
     b = bench.star_sector_bytes(s, workloads.star_plan())
     assert 4 * 100_000 < b < 24 * 100_000
+
+
+def test_star3_sector_bytes_matches_row_by_row_count():
+    # the three-probe join's eq / between build filters, on a small SSB Q3.1-shaped schema
+    from paper_1709_00700_gb300 import datagen, workloads
+    s = datagen.star3_schema(3_001, seed=6)
+    plan = workloads.star3_plan()
+    b = bench.star_sector_bytes(s, plan)
+    assert b == _brute_sector_bytes(s, plan)
+    assert 4 * 3_001 < b < 20 * 3_001
