@@ -92,10 +92,11 @@ TUNE_GRID = {"lowcard": "grouped", "keyval": "grouped", "filter_agg": "filter_ag
              "filter_project": "filter_project", "star": "star", "keys3": "grouped", "star3": "star"}
 
 
-def tune(ctx, plan, name, reps=3):
+def tune(ctx, plan, name, reps=3, probe_orders=False):
     """Exhaustive search over the workload's variant grid (the grids of the
-    variant-selection suite); returns (best variant, its ms, grid size, s)."""
-    from paper_1709_00700_gb300 import autotune, suite
+    variant-selection suite); with probe_orders, then every HASH_PROBE order
+    under the best variant.  Returns (best variant, its ms, variants tried, s)."""
+    from paper_1709_00700_gb300 import autotune, pv, suite
     grid = suite.GRIDS[TUNE_GRID[name]]
     t0 = time.perf_counter()
     best, best_ms = None, float("inf")
@@ -110,7 +111,17 @@ def tune(ctx, plan, name, reps=3):
             if ms < best_ms:
                 best, best_ms = dict(v), ms
         m.close()
-    return best, best_ms, len(grid), time.perf_counter() - t0
+    tried = len(grid)
+    if probe_orders and len(plan.get("probes", [])) > 1:
+        vv = {k: x for k, x in best.items() if k != "build"}
+        m = autotune.Measurer(ctx, plan, build_ht=best.get("build") or "perfect", reps=reps)
+        for order in pv.probe_orders(plan)[1:]:
+            ms = m(dict(vv, probe_order=order))
+            tried += 1
+            if ms < best_ms:
+                best, best_ms = dict(best, probe_order=list(order)), ms
+        m.close()
+    return best, best_ms, tried, time.perf_counter() - t0
 
 
 def measured_peaks():
@@ -413,9 +424,14 @@ def run_pv(args):
     elif args.no_tune:
         var_kw = dict(TUNED[args.workload])
     else:
-        var_kw, ms, n, secs = tune(ctx, plan, args.workload)
-        tuning = {"grid": TUNE_GRID[args.workload], "variants": n, "best_ms": ms, "seconds": secs}
+        var_kw, ms, n, secs = tune(ctx, plan, args.workload, probe_orders=args.probe_orders)
+        tuning = {"grid": TUNE_GRID[args.workload] + (" + probe orders" if args.probe_orders else ""),
+                  "variants": n, "best_ms": ms, "seconds": secs}
     build_ht = var_kw.pop("build", None) or args.build_ht
+    plan_bytes = plan  # algorithmic bytes: the workload's own probe order, whatever order runs
+    order = var_kw.pop("probe_order", None)
+    if order is not None:
+        plan = pv.reorder_probes(plan, order)[0]
     var = pv.variant(**var_kw)
     hts = ctx.build_all(plan, pv.ht_variant(build_ht))
     res = ctx.run(plan, var, hts)
@@ -477,7 +493,7 @@ def run_pv(args):
     alg_bytes = w["bytes_per_row"] * rows
     upper_bytes = None
     if args.workload in ("star", "star3"):
-        upper_bytes, alg_bytes = alg_bytes, star_sector_bytes(tables, plan)
+        upper_bytes, alg_bytes = alg_bytes, star_sector_bytes(tables, plan_bytes)
     achieved = alg_bytes / (dom_ms / 1000.0) / 1e9
     # end to end through the C ABI with host buffers: H2D of the step's input
     # columns from pinned memory, the pipeline, D2H of the result
@@ -504,7 +520,7 @@ def run_pv(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic (seeded counter-based generator)",
         "config": {"workload": w["desc"], "rows": rows,
                    **({"groups": args.groups, "keys": args.dist} if args.workload == "keyval" else {}),
-                   "variant": dict(var_kw, build=build_ht),
+                   "variant": dict(var_kw, build=build_ht, **({"probe_order": list(order)} if order else {})),
                    "tuning": tuning,
                    "l2": ("hot: no flush between steps, the inputs stay in L2 (hot-L2 numbers)" if args.hot_l2 else
                           "flushed (2x L2 write, then discard) before every step, outside the timed events"),
@@ -532,7 +548,7 @@ def run_pv(args):
                            "peak_source": f"pv_atomic_peak: {rows} uniform random updates of {words} words "
                                           f"into {args.groups} slots, measured in this run"}
     if rank == 0 and not args.no_cpu_baseline:
-        rate, cores, n = cpu_oracle_rate(plan, tables, args.cpu_budget, rows, args.cpu_threads)
+        rate, cores, n = cpu_oracle_rate(plan_bytes, tables, args.cpu_budget, rows, args.cpu_threads)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"the whole {rows}-row table, {n} runs on {cores} threads"}
     if rank == 0:
@@ -554,6 +570,8 @@ def main():
     ap.add_argument("--groups", type=int, default=1000)
     ap.add_argument("--dist", default="uniform", choices=["uniform", "zipf"], help="keyval: key distribution")
     ap.add_argument("--variant", default="", help="JSON pv_variant fields (skips tuning)")
+    ap.add_argument("--probe-orders", action="store_true",
+                    help="join workloads: after the grid search, also try every HASH_PROBE order")
     ap.add_argument("--no-tune", action="store_true", help="use the built-in variant instead of tuning")
     ap.add_argument("--build-ht", default="perfect")
     ap.add_argument("--cpu-budget", type=float, default=10.0)

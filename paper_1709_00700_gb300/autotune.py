@@ -146,10 +146,15 @@ class Measurer:
         self.hts = []
 
     def __call__(self, v: dict) -> float:
-        """Median ms of the variant; inf when it has no instantiation."""
+        """Median ms of the variant; inf when it has no instantiation.  A
+        "probe_order" entry runs the probes in that order (pv.reorder_probes;
+        the builds are shared)."""
         ctx, torch = self.ctx, self.torch
+        v = dict(v)
+        order = v.pop("probe_order", None)
+        plan = self.plan if order is None else pv.reorder_probes(self.plan, order)[0]
         try:
-            res = ctx.run(self.plan, pv.variant(**v), self.hts)
+            res = ctx.run(plan, pv.variant(**v), self.hts)
             ctx.sync()
         except pv.PVError as e:
             if e.status in (-2, -1):
@@ -178,6 +183,13 @@ class Measurer:
         t = statistics.median(times)
         self.best = min(self.best, t)
         return t
+
+
+def probe_order_dim(plan: dict):
+    """HASH_PROBE order as a search dimension: ("probe_order", every order of
+    the plan's probes, its own first).  Orders whose rewritten plan has no
+    compiled shape measure as inf."""
+    return ("probe_order", pv.probe_orders(plan))
 
 
 def exhaustive(measure, dims, db: TimingDB | None = None, qid: str = ""):

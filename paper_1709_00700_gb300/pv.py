@@ -307,6 +307,59 @@ def resolve_strings(plan: dict, dicts: dict):
     return plan, sets
 
 
+# ---- HASH_PROBE order ----------------------------------------------------------
+def _remap_ref(r, new_pos):
+    if isinstance(r, (list, tuple)) and len(r) == 3 and r[0] == "payload":
+        return ["payload", new_pos[int(r[1])], int(r[2])]
+    return r
+
+
+def reorder_probes(plan: dict, order):
+    """The plan with its probes run in `order` (a permutation of the probe
+    indices): the order of the HASH_PROBE operations as a variant (every order
+    gives the same rows).  Payload references follow their probe.  When every
+    group key is a payload, the keys are listed by probe position, so orders
+    that only move the grouping dimensions reach the same compiled shape.
+    Returns (plan, key_perm): new key column j holds original key key_perm[j]."""
+    import copy
+    probes = plan.get("probes", [])
+    order = [int(o) for o in order]
+    if sorted(order) != list(range(len(probes))):
+        raise PVError(-1, f"probe order {order} is not a permutation of {len(probes)} probes")
+    new_pos = {old: new for new, old in enumerate(order)}
+    out = copy.deepcopy(plan)
+    out["probes"] = [copy.deepcopy(probes[o]) for o in order]
+    keys = [_remap_ref(r, new_pos) for r in plan.get("group_by", [])]
+    key_perm = list(range(len(keys)))
+    if keys and all(isinstance(r, list) and r[0] == "payload" for r in keys):
+        key_perm = sorted(key_perm, key=lambda i: (keys[i][1], keys[i][2]))
+        keys = [keys[i] for i in key_perm]
+    if "group_by" in plan:
+        out["group_by"] = keys
+    if "aggs" in plan:
+        out["aggs"] = [[a[0]] + ([[[t[0], _remap_ref(t[1], new_pos)] + list(t[2:]) for t in a[1]]] if len(a) > 1
+                                 else []) for a in plan["aggs"]]
+    if "project" in plan:
+        out["project"] = [_remap_ref(r, new_pos) for r in plan["project"]]
+    return out, key_perm
+
+
+def restore_key_order(cols, key_perm):
+    """Result columns of a reordered plan, with the key columns put back in the
+    original plan's order."""
+    nk = len(key_perm)
+    keys = [None] * nk
+    for new, old in enumerate(key_perm):
+        keys[old] = cols[new]
+    return keys + list(cols[nk:])
+
+
+def probe_orders(plan: dict) -> list:
+    """Every order of the plan's probes, the plan's own first."""
+    import itertools
+    return [tuple(o) for o in itertools.permutations(range(len(plan.get("probes", []))))]
+
+
 class Context:
     """One pv_ctx on a dedicated CUDA stream, allocating through torch."""
 
@@ -506,16 +559,24 @@ class Context:
     def free(self, handle: int):
         self._check(self.lib.pv_free(self.h, handle))
 
-    def query(self, plan: dict, var: pv_variant, htv: pv_ht_variant | None = None, keep: bool = False):
+    def query(self, plan: dict, var: pv_variant, htv: pv_ht_variant | None = None, keep: bool = False,
+              probe_order=None):
         """Builds, runs and fetches a whole plan; returns int64 result columns
-        (grouped results sorted by key, projections as produced).  String
-        predicates on dictionary-coded columns are resolved first."""
+        (grouped results sorted by key, projections as produced).  probe_order
+        runs the probes in that order (reorder_probes); the result keeps the
+        plan's column order.  String predicates on dictionary-coded columns are
+        resolved first."""
+        key_perm = None
+        if probe_order is not None:
+            plan, key_perm = reorder_probes(plan, probe_order)
         plan, sets = resolve_strings(plan, self.dicts)
         for name, codes in sets:
             self.register_table(name, {"code": codes})
         hts = self.build_all(plan, htv or ht_variant())
         res = self.run(plan, var, hts)
         cols = [c.astype(np.int64) for c in self.fetch(res)]
+        if key_perm is not None:
+            cols = restore_key_order(cols, key_perm)
         if not keep:
             self.free(res)
             for h in hts:

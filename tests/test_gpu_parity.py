@@ -836,3 +836,21 @@ def test_star3_region_filters_as_strings(ctx):
         for kind, kw in (("perfect", dict(agg="global", ht="perfect", pred="compacted", items_per_thread=1, block=512)),
                          ("linear", dict(agg="local", ht="perfect", pred="branch", items_per_thread=1, block=512))):
             assert_same(ctx.query(plan, pv.variant(**kw), pv.ht_variant(kind)), w, ctxmsg=f"{regions} {kind} {kw}")
+
+
+# ---------------------------------------------------------------- HASH_PROBE order
+def test_probe_orders_of_the_star_join(ctx):
+    s = _star_small(120_001, seed=41)
+    register(ctx, s)
+    plan = workloads.star_plan({"d_a": 60, "d_b": 50, "d_c": 30, "d_d": 40})
+    w = want(plan, s)
+    # the orders that keep the compiled shape: either pair of probes swapped (pv.reorder_probes)
+    for order in ((0, 1, 2, 3), (1, 0, 2, 3), (0, 1, 3, 2), (1, 0, 3, 2)):
+        for kind, kw in (("perfect", dict(agg="global", ht="perfect", pred="compacted", items_per_thread=1, block=512)),
+                         ("linear", dict(agg="local", ht="perfect", pred="branch", items_per_thread=1, block=512))):
+            got = ctx.query(plan, pv.variant(**kw), pv.ht_variant(kind), probe_order=order)
+            assert_same(got, w, ctxmsg=f"{order} {kind} {kw}")
+    with pytest.raises(pv.PVError) as e:  # a grouping dimension probed first: no compiled shape
+        ctx.query(plan, pv.variant(agg="global", ht="perfect", items_per_thread=1), pv.ht_variant("perfect"),
+                  probe_order=(2, 0, 1, 3))
+    assert e.value.status == -2
