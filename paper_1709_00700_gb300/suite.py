@@ -411,7 +411,7 @@ def confirm(data: SuiteData, ex: dict, summary: dict, reps: int = 15, top: int =
     configuration against the fastest of them.  The exploration's own best is
     the minimum of many 3-run medians (biased low by selection) and, for
     queries of tens of microseconds, of times quantised by the event timer;
-    re-timing the candidates removes both effects from the judgement."""
+    re-timing the candidates removes both effects from the assessment."""
     t0 = time.time()
     qmap = {q["id"]: q for q in ex["queries"]}
     rows = []
