@@ -103,3 +103,18 @@ def test_exhaustive_and_db_resume(tmp_path):
     db2 = autotune.TimingDB(str(tmp_path / "t.jsonl"))
     best2, ms2, _, _ = autotune.exhaustive(cost, _dims(), db2, "q1")
     assert best2 == best and n[0] == 24  # all timings came from the database
+
+
+def test_algorithm_1_searches_the_probe_order_dimension():
+    # a synthetic cost: block 512 is best, and only two probe orders have a compiled shape
+    from paper_1709_00700_gb300 import autotune, workloads
+    plan = workloads.star_plan()
+    dims = [("block", [256, 512, 1024]), autotune.probe_order_dim(plan)]
+    good = {(0, 1, 2, 3): 2.0, (1, 0, 3, 2): 1.5}
+
+    def cost(v):
+        return good.get(tuple(v["probe_order"]), float("inf")) * (1.0 if v["block"] == 512 else 1.3)
+
+    v, c, n = autotune.feature_wise(cost, dims)
+    assert v == {"block": 512, "probe_order": (1, 0, 3, 2)} and c == 1.5
+    assert n <= 3 + 24 + 3 + 24
