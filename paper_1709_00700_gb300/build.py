@@ -24,6 +24,21 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", 
          "-I" + INCLUDE, "-I" + CSRC, "--expt-relaxed-constexpr"]
 
 
+def source_hash() -> str:
+    """Short hash of the kernel sources (csrc/ and include/pv.h): measurement
+    records taken on other sources are reported as stale."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(CSRC)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            with open(os.path.join(CSRC, f), "rb") as fh:
+                h.update(fh.read())
+    with open(os.path.join(INCLUDE, "pv.h"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def nvcc() -> str:
     for cand in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", shutil.which("nvcc")):
         if cand and os.path.exists(cand):

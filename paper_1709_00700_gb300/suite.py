@@ -509,6 +509,7 @@ def main(argv=None):
     ap.add_argument("--confirm-reps", type=int, default=15, help="re-timing runs per candidate (0 = skip)")
     ap.add_argument("--restat", action="store_true", help="with --timings-in: recompute the queries' statistics")
     ap.add_argument("--online", action="store_true", help="also run the run-time re-tuning experiment")
+    ap.add_argument("--summary-out", default="", help="compact record of the figures (no per-query rows)")
     a = ap.parse_args(argv)
     ctx = pv.Context(0)
     if a.graphs:
@@ -542,15 +543,46 @@ def main(argv=None):
     if a.out:
         with open(a.out, "w") as f:
             json.dump(summary, f)
+    if a.summary_out:
+        with open(a.summary_out, "w") as f:
+            json.dump(compact_record(summary, a, argv), f, indent=1)
     ctx.close()
 
 
+def compact_record(summary: dict, args, argv=None) -> dict:
+    """The suite's figures without per-query rows: how it was run (command,
+    seed, sizes, grids, kernel sources), the network's and Algorithm 1's
+    within-10% fractions and geometric-mean slowdowns on the held-out queries
+    (against the exploration's timings and, when run, confirmed by re-timing),
+    and the run-time re-tuning experiment when run."""
+    import sys
+    from . import build
+    keep = ("queries", "train", "held_out", "grid_sizes", "exploration_s", "train_s", "train_rows", "chosen",
+            "validation", "mlp_within_10pct", "mlp_geomean_slowdown", "mlp_worst_slowdown",
+            "mlp_top3_within_10pct", "alg1_within_10pct", "alg1_geomean_slowdown", "alg1_worst_slowdown",
+            "alg1_variants_run", "alg1_configs")
+    rec = {"command": "python -m paper_1709_00700_gb300.suite " + " ".join(argv if argv is not None else sys.argv[1:]),
+           "seed": 1709, "rows": [args.min_rows, args.max_rows], "reps": args.reps,
+           "kernel_source_hash": build.source_hash(),
+           "explored": {k: summary[k] for k in keep if k in summary}}
+    if "confirmed" in summary:
+        rec["confirmed"] = {k: v for k, v in summary["confirmed"].items() if k != "per_query"}
+    if "online" in summary:
+        rec["online"] = summary["online"]
+    return rec
 
-def graph_experiment(ctx: "pv.Context", n_queries: int = 64, rows: int = 1_000_000, reps: int = 20) -> dict:
+
+
+def graph_experiment(ctx: "pv.Context", n_queries: int = 64, rows: int = 1_000_000, reps: int = 20,
+                     star_results: bool = False) -> dict:
     """CUDA graphs for many small pipelines: n_queries filter/aggregate queries
     (different constants, one shape) on a rows-row table replayed eagerly
     (one pv_rerun each) and as one captured graph; and a star join's four
-    build pipelines plus its probe pipeline, eager and as one graph."""
+    build pipelines plus its probe pipeline, eager and as one graph.  Every
+    graph replay must leave the same results as the eager runs (asserted);
+    with star_results the star join's result columns after the graph
+    replays are returned too (key-sorted, int64), for a check against the
+    oracle on datagen.star_schema(rows)."""
     import torch
     dev = f"cuda:{ctx.device}"
     u = datagen.uniform_int_torch
@@ -603,20 +635,32 @@ def graph_experiment(ctx: "pv.Context", n_queries: int = 64, rows: int = 1_000_0
             ctx.rebuild(h)
         ctx.rerun(res)
 
+    def star_cols():
+        cols = [c.astype(np.int64) for c in ctx.fetch(res)]
+        order = np.lexsort((cols[1], cols[0]))
+        return [c[order] for c in cols]
+
     star_e = timed(star_eager)
     ctx.sync()
+    want_star = star_cols()
     ctx._check(ctx.lib.pv_graph_capture_begin(ctx.h))
     star_eager()
     g = ctypes_graph_end(ctx)
     star_g = timed(lambda: ctx._check(ctx.lib.pv_graph_launch(ctx.h, g)))
     ctx.sync()
+    got_star = star_cols()
+    assert all(np.array_equal(a, b) for a, b in zip(got_star, want_star)) and len(got_star) == len(want_star), \
+        "graph replay of the star builds + probe changed its result"
     ctx.free(g)
     ctx.free(res)
     for h in hts:
         ctx.free(h)
-    return {"queries": n_queries, "rows": rows, "eager_ms": eager, "graph_ms": graph,
-            "eager_us_per_query": 1000 * eager / n_queries, "graph_us_per_query": 1000 * graph / n_queries,
-            "star_build_probe_rows": rows, "star_eager_ms": star_e, "star_graph_ms": star_g}
+    out = {"queries": n_queries, "rows": rows, "eager_ms": eager, "graph_ms": graph,
+           "eager_us_per_query": 1000 * eager / n_queries, "graph_us_per_query": 1000 * graph / n_queries,
+           "star_build_probe_rows": rows, "star_eager_ms": star_e, "star_graph_ms": star_g}
+    if star_results:
+        out["star_cols"] = got_star
+    return out
 
 
 def ctypes_graph_end(ctx) -> int:

@@ -53,11 +53,18 @@ def test_lowcard_grouped_6m_rows(ctx):
     plan = workloads.lowcard_plan()
     w = _oracle(plan, li)
     for kw in (dict(agg="local", ht="perfect", threads_per_table=1, pred="predicated", items_per_thread=1,
-                    block=256, prefetch=1),   # the benchmark's variant
+                    block=256, prefetch=1),   # the built-in variant (bench --no-tune)
+               dict(agg="local", ht="perfect", threads_per_table=1, pred="predicated", items_per_thread=1,
+                    block=256, prefetch=0),   # the variant the tuner picked in the last recorded bench run
                dict(agg="local", ht="perfect", pred="branch", items_per_thread=1, block=512),
                dict(agg="global", ht="linear", pred="predicated", items_per_thread=1),
                dict(agg="local", ht="cuckoo", exec="multi", items_per_thread=1)):
         assert_same(ctx.query(plan, pv.variant(**kw)), w, ctxmsg=str(kw))
+    # whatever variant the benchmark's exhaustive tuning picks on this GPU, in its launch configuration
+    import bench
+    best, _, _, _ = bench.tune(ctx, plan, "lowcard")
+    kw = {k: v for k, v in best.items() if k != "build"}
+    assert_same(ctx.query(plan, pv.variant(**kw)), w, ctxmsg=f"tuned {kw}")
 
 
 def _keyval_60m(ctx, g, dist):
@@ -83,6 +90,17 @@ def _keyval_60m(ctx, g, dist):
     (1_000_000, "zipf", [dict(agg="global", ht="perfect", pred="branch", items_per_thread=1, block=256),
                          dict(agg="global", ht="perfect", pred="branch", items_per_thread=1, block=256, warp_agg=1),
                          dict(agg="global", ht="cuckoo", exec="multi", items_per_thread=1)]),
+    # 1e7 groups: the global tables (240 MB perfect array, 1 GB linear table) no longer fit in L2
+    (10_000_000, "uniform", [dict(agg="global", ht="perfect", pred="branch", items_per_thread=1, block=256),
+                             dict(agg="global", ht="perfect", pred="predicated", items_per_thread=1, block=256,
+                                  prefetch=1),
+                             dict(agg="global", ht="linear", pred="branch", items_per_thread=1, block=256),
+                             dict(agg="global", ht="linear", exec="multi", items_per_thread=1)]),
+    (10_000_000, "zipf", [dict(agg="global", ht="perfect", pred="branch", items_per_thread=1, block=256),
+                          dict(agg="global", ht="perfect", pred="branch", items_per_thread=1, block=256,
+                               warp_agg=1),
+                          dict(agg="global", ht="linear", pred="predicated", items_per_thread=1, warp_agg=1),
+                          dict(agg="global", ht="cuckoo", exec="multi", items_per_thread=1)]),
 ])
 def test_keyval_60m_rows(ctx, g, dist, variants):
     host, keep = _keyval_60m(ctx, g, dist)

@@ -3,15 +3,18 @@
 pv_filter_project_noalloc serves callers that cannot allocate device memory
 (their device memory belongs to another allocator, or they cannot pay for
 cudaMalloc's synchronisation): its scratch is a static device array.  Its
-output must equal the multi-pass projection of pv_run_pipeline exactly, on
-consecutive calls that reuse the one scratch array.  This file is collected
-last so that a failure here leaves every other test already run.
+output must equal the multi-pass projection of pv_run_pipeline exactly, and
+the oracle's rows in input order, on consecutive calls that reuse the one
+scratch array; with too small an output it reports the overflow and keeps
+the first rows that fit.  This file is collected last so that a failure here
+leaves every other test already run.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+from oracle import oracle
 from paper_1709_00700_gb300 import datagen, pv, workloads
 
 pytestmark = pytest.mark.gpu
@@ -61,7 +64,27 @@ def test_noalloc_matches_multi_pass_projection_on_consecutive_calls():
         assert got[0].dtype == np.int32 and got[1].dtype == np.int64
         assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
         assert len(want[0]) > 0
+        exact = oracle.run(plan, {"t": t})["cols"]  # input order
+        assert np.array_equal(got[0].astype(np.int64), exact[0]) and np.array_equal(got[1], exact[1])
     ctx.close()
+
+
+def test_noalloc_reports_overflow_and_keeps_the_first_rows():
+    import torch
+    n = 200_001
+    t = datagen.table_filter_agg(n, seed=78)
+    dev = {c: torch.from_numpy(v).cuda() for c, v in t.items()}
+    lib = pv.load()
+    stream = torch.cuda.current_stream()
+    plan = workloads.filter_project_plan(10, 20, 40)
+    exact = oracle.run(plan, {"t": t})["cols"]
+    matches = len(exact[0])
+    assert matches > 100
+    for cap in (matches // 2, 0, matches):
+        status, got = _noalloc(lib, dev, n, (-2**63, 9, 20, 40), cap, stream)
+        assert status == (-7 if cap < matches else 0)
+        assert len(got[0]) == cap  # *out_count = min(matches, capacity)
+        assert np.array_equal(got[0].astype(np.int64), exact[0][:cap]) and np.array_equal(got[1], exact[1][:cap])
 
 
 def test_noalloc_rejects_sizes_beyond_its_maximum():
