@@ -53,7 +53,16 @@ WORKLOADS = {
                   desc="SUM(val), COUNT(*) GROUP BY a, b, c (16 x 64 x 7 groups), 60M rows"),
     "star3": dict(rows=60_000_000, bytes_per_row=3 * 4 + 8,
                   desc="three-probe star join (SSB Q3.1 shape) grouped on three dimension attributes, 60M fact rows"),
+    "q5": dict(rows=60_000_000, bytes_per_row=4 + 8 + 8,
+               desc="TPC-H Q5-shaped query of four pipelines (builds over two projection results, an aggregation "
+                    "over an aggregation) replayed as one CUDA graph, 60M line items, 15M orders, 1.5M customers"),
 }
+
+# Variant of each step of the multi-pipeline query (the last step reads a
+# grouped result, so it runs on the generic kernels).
+Q5_VARIANTS = {"cust": dict(exec="single", items_per_thread=1), "ord": dict(exec="single", items_per_thread=1),
+               "nat": dict(agg="local", ht="perfect", items_per_thread=1, block=512),
+               "region": dict(agg="global", ht="perfect")}
 
 # Variant per workload (measured best so far; the autotuner refreshes these).
 TUNED = {
@@ -422,15 +431,20 @@ def run_reference(args):
         return 0
     w = WORKLOADS[args.workload]
     rows = args.rows or w["rows"]
-    tables, plan = make_tables(args.workload, rows, args.groups, args.dist)
     from oracle import oracle
+    if args.workload == "q5":
+        tables, chain = datagen.tpch_schema(rows), workloads.q5_chain()
+        evaluate = lambda: oracle.run_chain(chain, tables, nthreads=cores)  # noqa: E731
+    else:
+        tables, plan = make_tables(args.workload, rows, args.groups, args.dist)
+        evaluate = lambda: oracle.run(plan, tables, nthreads=cores)  # noqa: E731
     cores = args.cpu_threads or oracle.hardware_threads()
     for _ in range(args.warmup):
-        oracle.run(plan, tables, nthreads=cores)
+        evaluate()
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.run(plan, tables, nthreads=cores)
+        evaluate()
         times.append(time.perf_counter() - t0)
     total = sum(times)
     value = rows * args.steps / total
@@ -603,6 +617,149 @@ def run_pv(args):
     return 0
 
 
+def run_pv_chain(args):
+    """The multi-pipeline query (workloads.q5_chain): every step's builds and
+    pipeline recorded as one CUDA graph; one bench step = one replay of the
+    graph (the whole query, line items as the rows)."""
+    import torch
+
+    from paper_1709_00700_gb300 import pv
+    rank, world, local = dist_env()
+    dist = init_dist(world)
+    torch.cuda.set_device(local)
+    w = WORKLOADS["q5"]
+    rows = args.rows or w["rows"]
+    tables, chain = datagen.tpch_schema(rows), workloads.q5_chain()
+    ctx = pv.Context(local)
+    dev = {t: {c: torch.from_numpy(np.ascontiguousarray(v)).cuda(local) for c, v in cols.items()}
+           for t, cols in tables.items()}
+    for t, cols in dev.items():
+        ctx.register_table(t, cols)
+    variants = json.loads(args.variant) if args.variant else Q5_VARIANTS
+    ch = ctx.run_chain(chain, {k: pv.variant(**v) for k, v in variants.items()}, pv.ht_variant(args.build_ht))
+    ctx.sync()
+    stream = ctx.stream
+    flush = (lambda: None) if args.hot_l2 else (lambda: ctx.lib.pv_l2_flush(ctx.h))
+    # per-step kernel times (eager, kernels bracketed by events): the pipeline kernels of every step
+    ctx.set_kernel_timing(True)
+    step_kernels = {name: [] for name, _, _ in ch.steps}
+    for _ in range(3):
+        flush()
+        for name, hts, res in ch.steps:
+            for h in hts:
+                ctx.rebuild(h)
+            ctx.rerun(res)
+            step_kernels[name].append(ctx.kernel_times())
+    ctx.set_kernel_timing(False)
+
+    def timed(fn, n):
+        ms = []
+        for _ in range(n):
+            flush()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return ms
+
+    eager_ms = timed(ch.rerun, max(3, min(args.steps, 20)))
+    ch.capture()
+    for _ in range(max(args.warmup, 1)):
+        flush()
+        ch.launch()
+    ctx.sync()
+    launches = sum(1 for _ in ch.steps)  # one graph launch per step, holding every kernel of the query
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(dist)
+    torch.cuda.synchronize()
+    try:
+        nv = NvmlSampler(local)
+    except OSError:
+        nv = None
+    if nv:
+        nv.__enter__()
+    for i in range(args.steps):
+        flush()
+        starts[i].record(stream)
+        ch.launch()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    if nv:
+        nv.__exit__()
+    barrier(dist)
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    total_s = max_over_ranks(dist, sum(step_ms) / 1000.0)
+    value = rows * world * args.steps / total_s
+    # roofline of the dominant kernel: the line-item pipeline's aggregation
+    nat = np.array(step_kernels["nat"], dtype=np.float64)
+    dom_ms = float(nat[:, int(np.argmax(nat.mean(axis=0)))].mean())
+    ord_cols = [c for c in ch.fetch(1)]
+    host = {"lineitem": tables["lineitem"], "ord": {"orderkey": ord_cols[0], "nation": ord_cols[1]}}
+    nat_plan = chain[2]["plan"]
+    alg_bytes = sector_bytes(host, nat_plan)
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / (dom_ms / 1000.0) / 1e9
+    # end to end: H2D of every input table from pinned memory, the graph, D2H of the final result
+    pinned = {t: {c: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for c, v in cols.items()}
+              for t, cols in tables.items()}
+    h2d = sum(v.numel() * v.element_size() for cols in pinned.values() for v in cols.values())
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        with torch.cuda.stream(stream):
+            for t, cols in pinned.items():
+                for c, v in cols.items():
+                    dev[t][c].copy_(v, non_blocking=True)
+        ch.launch()
+        out = ch.fetch()
+        d2h = sum(a.nbytes for a in out) + 8
+    e2e_s = max_over_ranks(dist, time.perf_counter() - t0)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic (seeded counter-based generator)",
+        "config": {"workload": w["desc"], "rows": rows, "variants": variants, "build": args.build_ht,
+                   "l2": ("hot: no flush between steps" if args.hot_l2 else
+                          "flushed (2x L2 write, then discard) before every step, outside the timed events"),
+                   "seed": datagen.DEFAULT_SEED, "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "line-item pipeline (step nat), its longest kernel",
+                     "kernel_ms": dom_ms, "algorithmic_bytes": alg_bytes, "peak_source": f"{peak_kind} hbm_gbs",
+                     "algorithmic_bytes_note": "sector-exact bytes of the line-item pipeline"},
+        "graph": {"graph_ms": float(np.median(step_ms)), "eager_ms": float(np.median(eager_ms)),
+                  "step_kernel_ms": {k: [float(x) for x in np.mean(np.array(v, dtype=np.float64), axis=0)]
+                                     for k, v in step_kernels.items()}},
+        "e2e": {"value": rows * world * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches * args.steps,
+        "clocks": nv.summary() if nv and nv.samples else {"sm_mhz": None, "reasons": ["unsampled"]},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle import oracle
+        cores = args.cpu_threads or oracle.hardware_threads()
+        oracle.run_chain(chain, tables, nthreads=cores)
+        t0, n = time.perf_counter(), 0
+        while True:
+            oracle.run_chain(chain, tables, nthreads=cores)
+            n += 1
+            if time.perf_counter() - t0 >= args.cpu_budget or n >= 50:
+                break
+        el = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": rows * n / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"the whole query over {rows} line items, {n} runs on {cores} threads"}
+    if rank == 0:
+        print(json.dumps(line))
+    ch.free()
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -626,7 +783,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    return run_reference(args) if args.impl == "reference" else run_pv(args)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_pv_chain(args) if args.workload == "q5" else run_pv(args)
 
 
 if __name__ == "__main__":

@@ -23,8 +23,9 @@
  *     kernels detect (table full, cuckoo cycle, key out of range, duplicate
  *     build key, output overflow) are recorded in a device error word and
  *     returned by the next pv_sync(), pv_result_shape() or pv_fetch_result().
- *   - No call falls back to the CPU: a shape or variant with no compiled
- *     instantiation returns PV_ERR_UNSUPPORTED.
+ *   - No call falls back to the CPU.  A pipeline whose shape has no compiled
+ *     kernel runs on the generic GPU kernels; a variant axis that the chosen
+ *     kernels do not implement returns PV_ERR_UNSUPPORTED.
  *   - A ctx is not thread-safe; use one ctx per host thread.
  */
 #ifndef PV_H
@@ -41,7 +42,7 @@ typedef int32_t pv_status;
 enum {
   PV_OK = 0,
   PV_ERR_INVALID_ARG = -1,      /* bad handle, size, alignment or spec */
-  PV_ERR_UNSUPPORTED = -2,      /* no compiled instantiation for this shape/variant */
+  PV_ERR_UNSUPPORTED = -2,      /* beyond a documented limit, or a variant axis the kernels lack */
   PV_ERR_HT_FULL = -3,          /* linear-probing table or local table chain exhausted */
   PV_ERR_CUCKOO_CYCLE = -4,     /* cuckoo eviction chain exceeded its bound */
   PV_ERR_KEY_OUT_OF_RANGE = -5, /* perfect-array key outside the declared domain */
@@ -66,7 +67,7 @@ typedef int32_t pv_graph; /* captured-graph handle */
 #define PV_MAX_AGGS 8
 #define PV_MAX_TERMS 3
 #define PV_MAX_PROJ 4
-#define PV_MAX_PAYLOAD 1
+#define PV_MAX_PAYLOAD 4
 
 /* FILTER comparison (Table 1): column op constant, or lo <= column <= hi.
  * PV_PREFIX (string starts with a constant) is for pv_dict_range only; a
@@ -89,9 +90,12 @@ typedef struct { pv_ht ht; pv_col fk; } pv_probe;
 
 /* Build pipeline (Table 2): LOOP over the key column's table, FILTER by the
  * conjunction of preds, HASH_PUT key -> payload columns.  Key and payload
- * columns are int32 (PV_I32) or uint8 (PV_U8) and have the same row count;
- * a table slot is 64 bits (32-bit key, 32-bit payload), so at most one
- * payload column. */
+ * columns are int32 (PV_I32) or uint8 (PV_U8) and have the same row count.
+ * A table slot is 64 bits (32-bit key, 32 bits of payload): with one payload
+ * column the slot holds its value; with two to four, the slot holds the build
+ * row and a probe gathers the payload values from the payload columns (which
+ * must then stay alive and unchanged while pipelines probe the table; such
+ * tables are probed by the generic kernels). */
 typedef struct {
   pv_col key;
   int32_t n_preds;
@@ -122,10 +126,11 @@ typedef struct {
  *   otherwise               AGGREGATE(aggs)
  * All fact columns referenced must have the same row count.
  * Group keys (the attribute set G of HASH_AGGREGATE, Table 1): one part of any
- * column type; two 32-bit parts (packed into one 64-bit key); or three parts
- * (a composite key: each part minus its minimum, in mixed radix over the
- * parts' value spans taken from column or build-payload statistics; the
- * product of the spans must be at most 2^40, else PV_ERR_UNSUPPORTED). */
+ * column type; two 32-bit parts (packed into one 64-bit key); or three parts,
+ * or two of which one is 64 bits wide (a composite key: each part minus its
+ * minimum, in mixed radix over the parts' value spans taken from column or
+ * build-payload statistics; the product of the spans must be at most 2^40,
+ * else PV_ERR_UNSUPPORTED). */
 typedef struct {
   int32_t n_preds;
   pv_pred preds[PV_MAX_PREDS];
@@ -172,6 +177,14 @@ typedef struct {
                                 the same group key first combine their aggregates (match_any), one lane
                                 updates the table (Section 4's local pre-aggregation applied within a
                                 warp); 0 = every row updates.  Shared-memory (local) tables ignore it. */
+  int32_t interp;            /* 0: the kernel compiled for the pipeline's shape when one exists, else the
+                                generic kernels; 1: always the generic kernels, which read the pipeline
+                                program (predicates, probes, key parts, aggregate terms, projected values)
+                                at run time, one row per thread.  The generic kernels implement the
+                                branched and predicated modes, grid-stride access, single and multi pass,
+                                and global or CTA-local tables; the other axes (chunked access, compacted
+                                mode, thread-private and cluster tables, warp pre-aggregation) return
+                                PV_ERR_UNSUPPORTED there. */
   uint64_t seed;             /* aggregation hash seeds */
 } pv_variant;
 
@@ -220,7 +233,12 @@ pv_status pv_rebuild_hash_table(pv_ctx* ctx, pv_ht ht);
 /* ---- probe / scan pipelines --------------------------------------------- */
 
 /* Enqueues the pipeline program under the variant and returns a ctx-owned
- * result handle.  Allocates the result (and scratch) before enqueueing. */
+ * result handle.  Allocates the result (and scratch) before enqueueing.
+ * Every spec within the limits above runs: on the kernel compiled for its
+ * shape, or else on the generic kernels (see pv_variant.interp).  Limits that
+ * return PV_ERR_UNSUPPORTED: more than 8 distinct fact columns; a group key of
+ * three parts (or of two, one 64 bits wide) whose parts' value spans multiply
+ * to more than 2^40; a variant axis the chosen kernels do not implement. */
 pv_status pv_run_pipeline(pv_ctx* ctx, const pv_pipeline_spec* spec, const pv_variant* var,
                           pv_res* out);
 /* Enqueues the same pipeline again into the same result buffers (clearing
@@ -250,6 +268,31 @@ pv_status pv_fetch_result(pv_ctx* ctx, pv_res res, int32_t col, void* dst, int64
  * copies are enqueued together and the call synchronises once. */
 pv_status pv_fetch_results(pv_ctx* ctx, pv_res res, int32_t n_cols, void* const* dst, const int64_t* dst_rows,
                            int32_t dst_on_device);
+/* Registers result column `col` of pipeline result `res` as a column of
+ * table `table` (a pipeline's output feeding a later pipeline: a build over a
+ * probe pipeline's result, or an aggregation over an earlier aggregation).
+ * The column is the result's own device buffer, BORROWED from the result, so
+ * it reflects every rerun of the result (also inside a captured graph), and
+ * its row count is read on the device by each kernel that reads it, when
+ * that kernel runs: a later pipeline or build enqueued behind the producing
+ * pipeline on the ctx stream sees the rows it produced.  Column statistics
+ * (perfect-array domains) are those of the column's source: the projected
+ * fact column, the probed table's payload, or the group-key part; an
+ * aggregate column's are computed from the rows present when first needed.
+ * Pipelines over such columns run on the generic kernels; all their fact
+ * columns must come from the same result.  pv_free(res) also forgets the
+ * columns registered from it.  Errors: PV_ERR_INVALID_ARG for a bad handle or
+ * column index; PV_ERR_CUDA. */
+pv_status pv_register_result_column(pv_ctx* ctx, pv_res res, int32_t col, const char* table, const char* name,
+                                    pv_col* out);
+
+/* Which kernels a result runs on: *generic = 1 for the generic kernels, 0 for
+ * the kernel compiled for its shape; the shape's canonical signature (the
+ * fact column types by slot, predicate slots, probe key slots, key parts,
+ * aggregate terms and projected values) is copied NUL-terminated into
+ * buf[0..cap) when buf is non-NULL and cap > 0 (truncated to fit). */
+pv_status pv_result_kernel(pv_ctx* ctx, pv_res res, int32_t* generic, char* buf, int64_t cap);
+
 /* Releases a table, result or graph handle (columns: forgets the handle). */
 pv_status pv_free(pv_ctx* ctx, int32_t handle);
 

@@ -286,3 +286,17 @@ def run(plan: dict, tables: dict, nthreads: int = 1) -> dict:
         return {"kind": kind, "cols": cols, "overflow": bool(lib.or_result_flags(out) & 1)}
     finally:
         lib.or_result_free(out)
+
+
+def run_chain(chain: list, tables: dict, nthreads: int = 1) -> list:
+    """A query of several pipelines (paper_1709_00700_gb300.workloads.q5_chain
+    format): each step's plan is evaluated exactly, and its result columns
+    become table step["name"] for the later steps.  Returns every step's
+    result, in order."""
+    tables = dict(tables)
+    out = []
+    for step in chain:
+        res = run(step["plan"], tables, nthreads=nthreads)
+        tables[step["name"]] = dict(zip(step["columns"], res["cols"]))
+        out.append(res)
+    return out

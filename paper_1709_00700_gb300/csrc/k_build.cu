@@ -70,12 +70,23 @@ __device__ __forceinline__ void cuckoo_put(const DevHT& h, uint64_t val, int max
   set_error(err, PV_ERR_CUCKOO_CYCLE);
 }
 
+// One payload column: the slot holds its value.  Two or more: the slot holds
+// the build row, and probes gather the payload values from the columns.
+// Payload statistics (minimum and maximum of every payload column over the
+// surviving rows) feed the perfect-array domains of group keys on payloads.
 __global__ void k_build(const __grid_constant__ BuildParams bp) {
   const BuildInput& in = bp.in;
   const DevHT& h = bp.ht;
   unsigned long long* slots = reinterpret_cast<unsigned long long*>(h.slots);
-  uint64_t pmax = 0, pmin = 0;
-  for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < in.n_rows;
+  int64_t n = in.n_rows;
+  if (in.n_dyn != nullptr) {
+    const unsigned long long d = __ldcg(in.n_dyn);
+    n = d < static_cast<unsigned long long>(n) ? static_cast<int64_t>(d) : n;
+  }
+  uint64_t pmax[PV_MAX_PAYLOAD], pmin[PV_MAX_PAYLOAD];
+#pragma unroll
+  for (int i = 0; i < PV_MAX_PAYLOAD; ++i) pmax[i] = pmin[i] = 0;
+  for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < n;
        r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     bool pass = true;
     for (int i = 0; i < in.n_preds && pass; ++i) {
@@ -84,9 +95,17 @@ __global__ void k_build(const __grid_constant__ BuildParams bp) {
     }
     if (!pass) continue;
     const int64_t key = load_any(in.key, in.key_type, r);
-    const int32_t pay = in.n_payload ? static_cast<int32_t>(load_any(in.pay_col[0], in.pay_type[0], r)) : 0;
-    pmax = max(pmax, max_code(pay));
-    pmin = max(pmin, min_code(pay));
+    int32_t pay = 0;
+#pragma unroll
+    for (int i = 0; i < PV_MAX_PAYLOAD; ++i) {
+      if (i < in.n_payload) {
+        const int32_t v = static_cast<int32_t>(load_any(in.pay_col[i], in.pay_type[i], r));
+        if (i == 0) pay = v;
+        pmax[i] = max(pmax[i], max_code(v));
+        pmin[i] = max(pmin[i], min_code(v));
+      }
+    }
+    if (in.n_payload > 1) pay = static_cast<int32_t>(r);
     if (h.kind == PV_HT_PERFECT) {
       const int64_t i = key - h.kmin;
       if (static_cast<uint64_t>(i) >= static_cast<uint64_t>(h.cap)) {
@@ -107,11 +126,16 @@ __global__ void k_build(const __grid_constant__ BuildParams bp) {
     if (h.kind == PV_HT_LINEAR) linear_put(h, k32, val, bp.err);
     else cuckoo_put(h, val, bp.max_evictions, bp.err);
   }
-  pmax = warp_reduce<PV_MAX>(pmax);
-  pmin = warp_reduce<PV_MAX>(pmin);
-  if ((threadIdx.x & 31) == 0 && pmax) {
-    atomicMax(bp.pay_stats, static_cast<unsigned long long>(pmax));
-    atomicMax(bp.pay_stats + 1, static_cast<unsigned long long>(pmin));
+#pragma unroll
+  for (int i = 0; i < PV_MAX_PAYLOAD; ++i) {
+    if (i < in.n_payload) {
+      const uint64_t mx = warp_reduce<PV_MAX>(pmax[i]);
+      const uint64_t mn = warp_reduce<PV_MAX>(pmin[i]);
+      if ((threadIdx.x & 31) == 0 && mx) {
+        atomicMax(bp.pay_stats + 2 * i, static_cast<unsigned long long>(mx));
+        atomicMax(bp.pay_stats + 2 * i + 1, static_cast<unsigned long long>(mn));
+      }
+    }
   }
 }
 
@@ -195,21 +219,32 @@ pv_status build_table(const BuildEnv& env, const BuildInput& in, const pv_ht_var
     bytes = static_cast<size_t>(h.cap + 1) * 8;
   }
   const int max_ev = var.max_evictions > 0 ? var.max_evictions : 32 * std::max(1, h.log2cap);
+  if (in.n_payload > 1 && in.n_rows > INT32_MAX) {
+    msg = "tables with several payload columns index at most 2^31 - 1 build rows";
+    return PV_ERR_UNSUPPORTED;
+  }
   out.n_payload = in.n_payload;
+  out.indexed = in.n_payload > 1;
+  for (int i = 0; i < in.n_payload; ++i) {
+    out.pay_col[i] = in.pay_col[i];
+    out.pay_type[i] = in.pay_type[i];
+  }
   // [slots | 16-byte stats | presence bits (perfect arrays without payload or past 64 KB of slots: the
   // bits stay in L1 where the slots would not, and only hits read a slot)]
   const size_t stats_off = (bytes + 15) & ~size_t(15);
   const bool with_bits = var.kind == PV_HT_PERFECT && (in.n_payload == 0 || h.cap * 8 > (64 << 10));
   h.payload = in.n_payload > 0 ? 1 : 0;
   const size_t bits_bytes = with_bits ? static_cast<size_t>((h.cap + 31) / 32) * 4 : 0;
-  out.mem = env.alloc(stats_off + 16 + bits_bytes + 64, env.user);
+  constexpr size_t stats_bytes = 16 * PV_MAX_PAYLOAD;
+  out.mem = env.alloc(stats_off + stats_bytes + bits_bytes + 64, env.user);
   if (!out.mem) {
     msg = "allocator returned NULL";
     return PV_ERR_OOM;
   }
   h.slots = static_cast<uint64_t*>(out.mem);
   unsigned long long* stats = reinterpret_cast<unsigned long long*>(static_cast<char*>(out.mem) + stats_off);
-  h.bits = with_bits ? reinterpret_cast<const uint32_t*>(static_cast<char*>(out.mem) + stats_off + 16) : nullptr;
+  h.bits = with_bits ? reinterpret_cast<const uint32_t*>(static_cast<char*>(out.mem) + stats_off + stats_bytes)
+                      : nullptr;
   out.slot_bytes = bytes;
   BuildParams& bp = out.bp;
   bp = BuildParams{};
@@ -224,20 +259,20 @@ pv_status build_table(const BuildEnv& env, const BuildInput& in, const pv_ht_var
     return st;
   }
   cudaError_t e = cudaSuccess;
-  unsigned long long hs[2] = {0, 0};
-  e = cudaMemcpyAsync(hs, stats, 16, cudaMemcpyDeviceToHost, env.stream);
+  unsigned long long hs[2 * PV_MAX_PAYLOAD] = {};
+  e = cudaMemcpyAsync(hs, stats, stats_bytes, cudaMemcpyDeviceToHost, env.stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(env.stream);
   if (e != cudaSuccess) {
     msg = cudaGetErrorString(e);
     return PV_ERR_CUDA;
   }
-  if (in.n_payload) {
-    if (hs[0] == 0) {  // no surviving row
-      out.pay_min[0] = 0;
-      out.pay_max[0] = -1;
+  for (int i = 0; i < in.n_payload; ++i) {
+    if (hs[2 * i] == 0) {  // no surviving row
+      out.pay_min[i] = 0;
+      out.pay_max[i] = -1;
     } else {
-      out.pay_max[0] = decode_max(hs[0]);
-      out.pay_min[0] = decode_min(hs[1]);
+      out.pay_max[i] = decode_max(hs[2 * i]);
+      out.pay_min[i] = decode_min(hs[2 * i + 1]);
     }
   }
   return PV_OK;
@@ -247,7 +282,7 @@ pv_status rebuild_table(const BuildEnv& env, const BuildTable& t) {
   const BuildParams& bp = t.bp;
   const DevHT& h = bp.ht;
   cudaError_t e = cudaMemsetAsync(h.slots, h.kind == PV_HT_PERFECT ? 0 : 0xFF, t.slot_bytes, env.stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(bp.pay_stats, 0, 16, env.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bp.pay_stats, 0, 16 * PV_MAX_PAYLOAD, env.stream);
   if (e != cudaSuccess) return PV_ERR_CUDA;
   if (bp.in.n_rows > 0) {
     const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(env.sm_count * 8, (bp.in.n_rows + 255) / 256)));

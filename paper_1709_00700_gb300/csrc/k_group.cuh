@@ -651,7 +651,7 @@ __device__ __forceinline__ void extract_slots(const GroupDesc& gd, const GroupOu
     if (occ) {
       const int64_t pos = static_cast<int64_t>(base) + __popc(ball & ((1u << lane) - 1u));
       if (pos < g.out_cap) {
-        write_keys(gd, g, pos, perfect || gd.n_keys > 2, perfect ? static_cast<uint64_t>(s) : key);
+        write_keys(gd, g, pos, perfect || gd.coded, perfect ? static_cast<uint64_t>(s) : key);
         for (int a = 0; a < na; ++a) g.out[(gd.n_keys + a) * g.out_cap + pos] = decode_agg(gd.func[a], __ldcg(v + a));
       }
     }

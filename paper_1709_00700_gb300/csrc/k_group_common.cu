@@ -51,6 +51,7 @@ void register_group_join2();
 void register_group_join2y();
 void register_group_keys3();
 void register_group_star3();
+void register_group_q5();
 
 void register_group_shapes() {
   register_group_lowcard();
@@ -61,6 +62,7 @@ void register_group_shapes() {
   register_group_join2y();
   register_group_keys3();
   register_group_star3();
+  register_group_q5();
 }
 
 }  // namespace pv

@@ -390,6 +390,15 @@ static pv_status launch_agg_t(const LaunchCfg& c, const KParams& kp, const AggOu
   return cudaGetLastError() == cudaSuccess ? PV_OK : PV_ERR_CUDA;
 }
 
+pv_status launch_tile_scan(const LaunchCfg& c, const ProjOut& out, int32_t* err) {
+  kmark(c);
+  cudaError_t e = c.mark ? (k_tile_scan<<<1, 1024, 0, c.stream>>>(out, err), cudaSuccess)
+                         : pdl_launch(k_tile_scan, dim3(1), dim3(1024), 0, c.stream, out, err);
+  kmark(c);
+  ++*c.launches;
+  return e == cudaSuccess && cudaGetLastError() == cudaSuccess ? PV_OK : PV_ERR_CUDA;
+}
+
 template <class SH, bool P, bool C, int U>
 static pv_status launch_proj_t(const LaunchCfg& c, const KParams& kp, const ProjOut& out, int exec) {
   if (exec == PV_EXEC_SINGLE_PASS) {
@@ -492,7 +501,17 @@ using ShJoinCount = Shape<Cols<TI32>, Where<>, Probes<0>, Key<>, Aggs<Count>, Pr
 using ShJoinProj = Shape<Cols<TI32, TI64>, Where<>, Probes<0>, Key<>, Aggs<>, Proj<-1, 1>>;
 using ShFilterJoinProj = Shape<Cols<TI32, TI32, TI64>, Where<P<0>>, Probes<1>, Key<>, Aggs<>, Proj<-1, 2>>;
 
+// The projection steps of the TPC-H Q5-shaped multi-pipeline query: rows
+// that pass a probe, projected with their probe key (customers of the
+// selected nations: key, nation), and rows that pass a filter and a probe,
+// projected with the payload the probe binds (orders of the year: key, the
+// customer's nation).
+using ShProbeProjKey = Shape<Cols<TI32, TI32>, Where<>, Probes<0>, Key<>, Aggs<>, Proj<1, 0>>;
+using ShFilterProbeProjPay = Shape<Cols<TI32, TI32, TI32>, Where<P<0>>, Probes<1>, Key<>, Aggs<>, Proj<2, -1>>;
+
 void register_scan_shapes() {
+  reg_project<ShProbeProjKey>();
+  reg_project<ShFilterProbeProjPay>();
   reg_aggregate<ShJoinCount>();
   reg_aggregate<ShFilterAgg>();
   reg_project<ShFilterProj>();

@@ -75,9 +75,11 @@ struct Column {
   std::string table, name;
   int type;
   const void* ptr;
-  int64_t n_rows;
+  int64_t n_rows;                          // rows; for a result column its capacity
   bool has_stats = false;
   int64_t vmin = 0, vmax = 0;
+  const unsigned long long* n_dyn = nullptr;  // result column: row count on the device
+  int32_t src_res = 0;                     // result column: the result it belongs to
 };
 
 struct Canon {
@@ -96,15 +98,18 @@ struct Canon {
   int key_type[PV_MAX_KEYS]{};       // pv_type of the key part source
   int key_src_kind[PV_MAX_KEYS]{};   // PV_REF_COL or PV_REF_PAYLOAD
   int key_src[PV_MAX_KEYS][2]{};     // column handle | (probe, payload)
-  int64_t pay_min[PV_MAX_PROBES]{};  // payload statistics of each probed table
-  int64_t pay_max[PV_MAX_PROBES]{};
+  int64_t pay_min[PV_MAX_PROBES][PV_MAX_PAYLOAD]{};  // payload statistics of each probed table
+  int64_t pay_max[PV_MAX_PROBES][PV_MAX_PAYLOAD]{};
   int64_t capacity_hint = 0;
+  GenSpec gs{};               // the program as data, for the generic kernels
+  bool generic_only = false;  // no compiled shape can run it (see canonicalize)
 };
 
 struct Result {
   Canon canon;
   pv_variant var{};
   const ShapeEntry* entry = nullptr;
+  bool generic = false;  // runs on the generic kernels
   std::vector<void*> mem;
   AggOut agg{};
   ProjOut proj{};
@@ -211,8 +216,12 @@ void clamp_range(int type, int64_t& lo, int64_t& hi) {
 
 // Canonicalises a pipeline spec: assigns slots to the fact columns in order of
 // first use (predicates, probe keys, group keys, aggregate terms, projected
-// columns), merges predicates on one column into one range, and writes the
-// shape signature the compiled shapes are registered under.
+// columns), merges predicates on one column into one range, writes the shape
+// signature the compiled shapes are registered under, and the same program as
+// data (GenSpec) for the generic kernels.  Parts no compiled shape takes
+// (int64 probe keys, constant terms over payloads, two-part keys with a 64-bit
+// part, tables with several payload columns, result columns) mark the
+// program generic_only instead of failing.
 static pv_status canonicalize(pv_ctx* c, const pv_pipeline_spec* s, Canon& k) {
   if (!s) return fail(c, PV_ERR_INVALID_ARG, "null spec");
   if (s->n_preds < 0 || s->n_preds > PV_MAX_PREDS || s->n_probes < 0 || s->n_probes > PV_MAX_PROBES ||
@@ -226,7 +235,9 @@ static pv_status canonicalize(pv_ctx* c, const pv_pipeline_spec* s, Canon& k) {
   k.mode = s->n_proj > 0 ? MODE_PROJECT : s->n_keys > 0 ? MODE_GROUPED : MODE_AGGREGATE;
   k.n_rows = -1;
   k.capacity_hint = s->capacity_hint;
+  GenSpec& gs = k.gs;
   std::string err;
+  bool first_col = true;
   auto col_of = [&](pv_col h) -> const Column* {
     auto it = c->cols.find(h);
     return it == c->cols.end() ? nullptr : &it->second;
@@ -234,12 +245,19 @@ static pv_status canonicalize(pv_ctx* c, const pv_pipeline_spec* s, Canon& k) {
   auto slot = [&](pv_col h) -> int {
     const Column* col = col_of(h);
     if (!col) { err = "unknown column handle " + std::to_string(h); return -1; }
-    if (k.n_rows < 0) k.n_rows = col->n_rows;
-    else if (k.n_rows != col->n_rows) { err = "fact columns differ in row count"; return -1; }
+    if (first_col) {
+      k.n_rows = col->n_rows;
+      gs.n_dyn = col->n_dyn;
+      first_col = false;
+    } else if (k.n_rows != col->n_rows || gs.n_dyn != col->n_dyn) {
+      err = "fact columns differ in row count";
+      return -1;
+    }
     for (int i = 0; i < k.n_slots; ++i) if (k.slot_col[i] == h) return i;
     if (k.n_slots == kMaxSlots) { err = "more than 8 distinct fact columns"; return -2; }
     k.slot_col[k.n_slots] = h;
     k.slot_type[k.n_slots] = col->type;
+    gs.slot_type[k.n_slots] = col->type;
     k.kp.col[k.n_slots] = col->ptr;
     return k.n_slots++;
   };
@@ -262,34 +280,47 @@ static pv_status canonicalize(pv_ctx* c, const pv_pipeline_spec* s, Canon& k) {
     if (!merged) ranges.push_back({sl, {lo, hi}});
   }
   std::string sw = "|W:";
+  gs.n_preds = static_cast<int32_t>(ranges.size());
   for (size_t j = 0; j < ranges.size(); ++j) {
     int64_t lo = ranges[j].second.first, hi = ranges[j].second.second;
     clamp_range(k.slot_type[ranges[j].first], lo, hi);
     k.kp.lo[j] = lo;
     k.kp.hi[j] = hi;
+    gs.pred_slot[j] = ranges[j].first;
     sw += std::to_string(ranges[j].first) + ",";
   }
   // HASH_PROBE
   std::string sj = "|J:";
   std::vector<const BuildTable*> probe_tab;
+  gs.n_probes = s->n_probes;
   for (int j = 0; j < s->n_probes; ++j) {
     auto it = c->tables.find(s->probes[j].ht);
     if (it == c->tables.end()) return fail(c, PV_ERR_INVALID_ARG, "unknown hash table handle");
     int sl = slot(s->probes[j].fk);
     if (sl < 0) return bad(sl);
-    if (k.slot_type[sl] == PV_I64) return fail(c, PV_ERR_UNSUPPORTED, "int64 probe keys");
-    k.kp.probe[j] = it->second->ht;
-    k.pay_min[j] = it->second->n_payload ? it->second->pay_min[0] : 0;
-    k.pay_max[j] = it->second->n_payload ? it->second->pay_max[0] : -1;
-    probe_tab.push_back(it->second.get());
+    if (k.slot_type[sl] == PV_I64) k.generic_only = true;  // int64 probe keys
+    const BuildTable& bt = *it->second;
+    k.kp.probe[j] = bt.ht;
+    for (int b = 0; b < PV_MAX_PAYLOAD; ++b) {
+      k.pay_min[j][b] = b < bt.n_payload ? bt.pay_min[b] : 0;
+      k.pay_max[j][b] = b < bt.n_payload ? bt.pay_max[b] : -1;
+      gs.pay_col[j][b] = b < bt.n_payload ? bt.pay_col[b] : nullptr;
+      gs.pay_type[j][b] = b < bt.n_payload ? bt.pay_type[b] : PV_I32;
+    }
+    gs.indexed[j] = bt.indexed ? 1 : 0;
+    if (bt.indexed) k.generic_only = true;  // payloads gathered by build row
+    gs.probe_slot[j] = sl;
+    probe_tab.push_back(&bt);
     sj += std::to_string(sl) + ",";
   }
-  auto ref_sig = [&](const pv_ref& r, std::string& out, int* type) -> int {
+  // A value reference: its signature text, its type, its GenSpec form.
+  auto ref_sig = [&](const pv_ref& r, std::string& out, int* type, GRef* g) -> int {
     if (r.kind == PV_REF_COL) {
       int sl = slot(r.a);
       if (sl < 0) return sl;
       out += "x" + std::to_string(sl);
       if (type) *type = k.slot_type[sl];
+      if (g) *g = GRef{PV_REF_COL, sl, 0};
       return 0;
     }
     if (r.kind == PV_REF_PAYLOAD) {
@@ -299,6 +330,7 @@ static pv_status canonicalize(pv_ctx* c, const pv_pipeline_spec* s, Canon& k) {
       }
       out += "p" + std::to_string(r.a) + "." + std::to_string(r.b);
       if (type) *type = PV_I32;
+      if (g) *g = GRef{PV_REF_PAYLOAD, r.a, r.b};
       return 0;
     }
     err = "bad reference kind";
@@ -307,8 +339,9 @@ static pv_status canonicalize(pv_ctx* c, const pv_pipeline_spec* s, Canon& k) {
   // HASH_AGGREGATE keys
   std::string sk = "|K:";
   k.n_keys = s->n_keys;
+  gs.n_keys = s->n_keys;
   for (int i = 0; i < s->n_keys; ++i) {
-    int r = ref_sig(s->keys[i], sk, &k.key_type[i]);
+    int r = ref_sig(s->keys[i], sk, &k.key_type[i], &gs.key[i]);
     if (r < 0) return bad(r);
     sk += ",";
     k.key_src_kind[i] = s->keys[i].kind;
@@ -316,29 +349,41 @@ static pv_status canonicalize(pv_ctx* c, const pv_pipeline_spec* s, Canon& k) {
     k.key_src[i][1] = s->keys[i].b;
   }
   if (s->n_keys == 2 && (k.key_type[0] == PV_I64 || k.key_type[1] == PV_I64))
-    return fail(c, PV_ERR_UNSUPPORTED, "two-part group keys take 32-bit parts only");
+    k.generic_only = true;  // a two-part key with a 64-bit part is coded in mixed radix
   // Aggregates and ARITHMETIC terms
   std::string sa = "|A:";
   int nconst = 0;
   k.n_aggs = s->n_aggs;
+  gs.n_aggs = s->n_aggs;
   for (int i = 0; i < s->n_aggs; ++i) {
     const pv_agg& a = s->aggs[i];
     if (a.func < PV_SUM || a.func > PV_MAX) return fail(c, PV_ERR_INVALID_ARG, "bad aggregate function");
     k.agg_func[i] = a.func;
+    gs.agg[i].func = a.func;
+    gs.agg[i].n_terms = 0;
     if (a.func == PV_COUNT) { sa += "N,"; continue; }
     if (a.n_terms < 1 || a.n_terms > PV_MAX_TERMS) return fail(c, PV_ERR_INVALID_ARG, "aggregate needs 1..3 terms");
+    gs.agg[i].n_terms = a.n_terms;
     sa += a.func == PV_SUM ? "S(" : a.func == PV_MIN ? "m(" : "M(";
     for (int t = 0; t < a.n_terms; ++t) {
       const pv_term& tm = a.terms[t];
+      GTerm& gt = gs.agg[i].t[t];
+      gt.kind = tm.kind;
+      gt.c = tm.kind == PV_TERM_X ? 0 : tm.c;
       if (tm.kind == PV_TERM_X) {
-        int r = ref_sig(tm.x, sa, nullptr);
+        int r = ref_sig(tm.x, sa, nullptr, &gt.x);
         if (r < 0) return bad(r);
       } else if (tm.kind == PV_TERM_X_PLUS_C || tm.kind == PV_TERM_C_MINUS_X) {
-        if (tm.x.kind != PV_REF_COL) return fail(c, PV_ERR_UNSUPPORTED, "constant terms take fact columns only");
-        int sl = slot(tm.x.a);
-        if (sl < 0) return bad(sl);
-        sa += (tm.kind == PV_TERM_X_PLUS_C ? "xpc" : "cmx") + std::to_string(sl) + "#" + std::to_string(nconst);
-        k.kp.c[nconst++] = tm.c;
+        std::string ignore;
+        int r = ref_sig(tm.x, ignore, nullptr, &gt.x);
+        if (r < 0) return bad(r);
+        if (tm.x.kind != PV_REF_COL) {
+          k.generic_only = true;  // constant terms over payloads
+          sa += "?";
+        } else if (nconst < kMaxConsts) {
+          sa += (tm.kind == PV_TERM_X_PLUS_C ? "xpc" : "cmx") + std::to_string(gt.x.a) + "#" + std::to_string(nconst);
+          k.kp.c[nconst++] = tm.c;
+        }
       } else {
         return fail(c, PV_ERR_INVALID_ARG, "bad term kind");
       }
@@ -349,22 +394,29 @@ static pv_status canonicalize(pv_ctx* c, const pv_pipeline_spec* s, Canon& k) {
   // PROJECT
   std::string sp = "|P:";
   k.n_proj = s->n_proj;
+  gs.n_proj = s->n_proj;
   for (int i = 0; i < s->n_proj; ++i) {
-    if (s->proj[i].kind == PV_REF_PAYLOAD) {  // int32 payload of probe a
-      const pv_ref& r = s->proj[i];
-      if (r.a < 0 || r.a >= s->n_probes || r.b != 0 || r.b >= probe_tab[r.a]->n_payload)
+    const pv_ref& r = s->proj[i];
+    if (r.kind == PV_REF_PAYLOAD) {  // int32 payload b of probe a
+      if (r.a < 0 || r.a >= s->n_probes || r.b < 0 || r.b >= probe_tab[r.a]->n_payload)
         return fail(c, PV_ERR_INVALID_ARG, "bad payload reference");
-      sp += "p" + std::to_string(r.a) + ",";
+      sp += "p" + std::to_string(r.a) + (r.b ? "." + std::to_string(r.b) : std::string()) + ",";
+      gs.proj[i] = GRef{PV_REF_PAYLOAD, r.a, r.b};
       k.proj_type[i] = PV_I32;
+      gs.proj_type[i] = PV_I32;
       continue;
     }
-    if (s->proj[i].kind != PV_REF_COL) return fail(c, PV_ERR_INVALID_ARG, "bad projection reference");
-    int sl = slot(s->proj[i].a);
+    if (r.kind != PV_REF_COL) return fail(c, PV_ERR_INVALID_ARG, "bad projection reference");
+    int sl = slot(r.a);
     if (sl < 0) return bad(sl);
     sp += std::to_string(sl) + ",";
+    gs.proj[i] = GRef{PV_REF_COL, sl, 0};
     k.proj_type[i] = k.slot_type[sl];
+    gs.proj_type[i] = k.slot_type[sl];
   }
   if (k.n_rows < 0) return fail(c, PV_ERR_INVALID_ARG, "pipeline references no fact column");
+  if (gs.n_dyn != nullptr) k.generic_only = true;  // the row count is known on the device only
+  gs.n_slots = k.n_slots;
   std::string sc = "C:";
   for (int i = 0; i < k.n_slots; ++i)
     sc += k.slot_type[i] == PV_I32 ? "i32," : k.slot_type[i] == PV_I64 ? "i64," : "u8,";
@@ -413,7 +465,11 @@ static pv_status resolve_launch(pv_ctx* c, const pv_variant& v, LaunchCfg& L) {
 
 // Kernels of this translation unit: column statistics, L2 flush, watchdog spin.
 template <class T>
-__global__ void k_minmax(const T* p, int64_t n, unsigned long long* out) {
+__global__ void k_minmax(const T* p, int64_t n, const unsigned long long* n_dyn, unsigned long long* out) {
+  if (n_dyn != nullptr) {
+    const unsigned long long d = __ldcg(n_dyn);
+    n = d < static_cast<unsigned long long>(n) ? static_cast<int64_t>(d) : n;
+  }
   uint64_t mx = 0, mn = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t v = static_cast<int64_t>(p[i]);
@@ -520,15 +576,18 @@ static pv_status column_stats(pv_ctx* c, pv_col h, int64_t* mn, int64_t* mx) {
     PV_CUDA(c, cudaMemsetAsync(d, 0, 16, c->stream));
     const int grid = std::max(1, std::min<int>(c->sm_count * 4, static_cast<int>((col.n_rows + 255) / 256)));
     if (col.n_rows > 0) {
-      if (col.type == PV_I32) k_minmax<<<grid, 256, 0, c->stream>>>(static_cast<const int32_t*>(col.ptr), col.n_rows, d);
-      else if (col.type == PV_I64) k_minmax<<<grid, 256, 0, c->stream>>>(static_cast<const int64_t*>(col.ptr), col.n_rows, d);
-      else k_minmax<<<grid, 256, 0, c->stream>>>(static_cast<const uint8_t*>(col.ptr), col.n_rows, d);
+      const unsigned long long* nd = col.n_dyn;
+      if (col.type == PV_I32) k_minmax<<<grid, 256, 0, c->stream>>>(static_cast<const int32_t*>(col.ptr), col.n_rows, nd, d);
+      else if (col.type == PV_I64) k_minmax<<<grid, 256, 0, c->stream>>>(static_cast<const int64_t*>(col.ptr), col.n_rows, nd, d);
+      else k_minmax<<<grid, 256, 0, c->stream>>>(static_cast<const uint8_t*>(col.ptr), col.n_rows, nd, d);
       PV_CUDA(c, cudaGetLastError());
     }
-    unsigned long long hbuf[2];
+    unsigned long long hbuf[2] = {0, 0};
     PV_CUDA(c, cudaMemcpyAsync(hbuf, d, 16, cudaMemcpyDeviceToHost, c->stream));
     PV_CUDA(c, cudaStreamSynchronize(c->stream));
-    if (col.n_rows > 0) {
+    // some row was present: a row's max code and min code are not both 0 (that would need the
+    // value to be INT64_MIN and INT64_MAX at once)
+    if (col.n_rows > 0 && (hbuf[0] != 0 || hbuf[1] != 0)) {
       col.vmax = decode_max(hbuf[0]);
       col.vmin = decode_min(hbuf[1]);
     } else {
@@ -597,6 +656,7 @@ static pv_status alloc_result(pv_ctx* c, Result& r) {
     if (k.agg_func[i] == PV_COUNT) gd.count_word = i;
   for (int i = 0; i < k.n_aggs; ++i) gd.func[i] = k.agg_func[i];
   for (int i = 0; i < k.n_keys; ++i) gd.key64[i] = k.key_type[i] == PV_I64;
+  gd.coded = k.n_keys > 2 || (k.n_keys == 2 && (gd.key64[0] || gd.key64[1]));
   // Key domains from column statistics / build payload statistics.
   int64_t domain = 1;
   bool domain_ok = true;
@@ -606,8 +666,8 @@ static pv_status alloc_result(pv_ctx* c, Result& r) {
       pv_status s = column_stats(c, k.key_src[i][0], &mn, &mx);
       if (s != PV_OK) return s;
     } else {
-      mn = k.pay_min[k.key_src[i][0]];
-      mx = k.pay_max[k.key_src[i][0]];
+      mn = k.pay_min[k.key_src[i][0]][k.key_src[i][1]];
+      mx = k.pay_max[k.key_src[i][0]][k.key_src[i][1]];
     }
     if (mx < mn) { mn = 0; mx = 0; }  // empty source: any domain works
     gd.key_min[i] = mn;
@@ -618,8 +678,8 @@ static pv_status alloc_result(pv_ctx* c, Result& r) {
       domain *= gd.key_span[i];
     else domain_ok = false;
   }
-  if (k.n_keys > 2 && !domain_ok)
-    return fail(c, PV_ERR_UNSUPPORTED, "three-part group keys need a key domain of at most 2^40 codes");
+  if (gd.coded && !domain_ok)
+    return fail(c, PV_ERR_UNSUPPORTED, "composite group keys need a key domain of at most 2^40 codes");
   GroupOut& g = r.grp;
   g.ht = r.var.ht;
   g.hash = r.var.hash;
@@ -674,9 +734,16 @@ static pv_status launch_result(pv_ctx* c, Result& r) {
   r.rows_cached = -1;
   Canon& k = r.canon;
   k.kp.prefetch = r.var.prefetch;
-  if (k.mode == MODE_AGGREGATE) s = r.entry->aggregate(L, k.kp, r.agg);
-  else if (k.mode == MODE_PROJECT) s = r.entry->project(L, k.kp, r.proj, r.var.exec);
-  else s = r.entry->grouped(L, k.kp, r.gd, r.grp, r.var);
+  if (r.generic) {
+    if (k.mode == MODE_AGGREGATE) s = generic_aggregate(L, k.kp, k.gs, r.agg);
+    else if (k.mode == MODE_PROJECT) s = generic_project(L, k.kp, k.gs, r.proj, r.var.exec);
+    else s = generic_grouped(L, k.kp, k.gs, r.gd, r.grp, r.var);
+    if (s == PV_ERR_UNSUPPORTED) return fail(c, s, "the generic kernels do not implement this variant");
+  } else {
+    if (k.mode == MODE_AGGREGATE) s = r.entry->aggregate(L, k.kp, r.agg);
+    else if (k.mode == MODE_PROJECT) s = r.entry->project(L, k.kp, r.proj, r.var.exec);
+    else s = r.entry->grouped(L, k.kp, r.gd, r.grp, r.var);
+  }
   if (s == PV_ERR_UNSUPPORTED) return fail(c, s, "no instantiation of this shape for the variant");
   if (s != PV_OK) return fail(c, s, "kernel launch failed");
   return PV_OK;
@@ -763,6 +830,65 @@ pv_status pv_register_column(pv_ctx* c, const char* table, const char* name, int
   return PV_OK;
 }
 
+pv_status pv_register_result_column(pv_ctx* c, pv_res res, int32_t col, const char* table, const char* name,
+                                    pv_col* out) {
+  if (!c || !out) return PV_ERR_INVALID_ARG;
+  auto it = c->results.find(res);
+  if (it == c->results.end()) return fail(c, PV_ERR_INVALID_ARG, "unknown result handle");
+  Result& r = *it->second;
+  if (col < 0 || col >= r.n_cols) return fail(c, PV_ERR_INVALID_ARG, "column index out of range");
+  const Canon& k = r.canon;
+  Column nc;
+  nc.table = table ? table : "";
+  nc.name = name ? name : "";
+  nc.type = r.col_type[col];
+  nc.src_res = res;
+  // Statistics of the column's source: a projected fact column or payload keeps
+  // its source's value range, a group-key part its domain; aggregates are
+  // computed from the rows when first needed.
+  auto inherit = [&](int64_t lo, int64_t hi) {
+    nc.has_stats = true;
+    nc.vmin = lo;
+    nc.vmax = hi;
+  };
+  if (k.mode == MODE_PROJECT) {
+    nc.ptr = r.proj.col[col];
+    nc.n_rows = r.proj.capacity;
+    nc.n_dyn = reinterpret_cast<const unsigned long long*>(r.proj.count);
+    const GRef& g = k.gs.proj[col];
+    if (g.kind == PV_REF_PAYLOAD) {
+      inherit(k.pay_min[g.a][g.b], k.pay_max[g.a][g.b]);
+    } else {
+      int64_t lo, hi;
+      pv_status st = column_stats(c, k.slot_col[g.a], &lo, &hi);
+      if (st != PV_OK) return st;
+      inherit(lo, hi);
+    }
+  } else if (k.mode == MODE_GROUPED) {
+    nc.ptr = r.grp.out + static_cast<size_t>(col) * r.grp.out_cap;
+    nc.n_rows = r.grp.out_cap;
+    nc.n_dyn = r.grp.out_count;
+    if (col < k.n_keys) {
+      int64_t lo, hi;
+      if (k.key_src_kind[col] == PV_REF_COL) {
+        pv_status st = column_stats(c, k.key_src[col][0], &lo, &hi);
+        if (st != PV_OK) return st;
+      } else {
+        lo = k.pay_min[k.key_src[col][0]][k.key_src[col][1]];
+        hi = k.pay_max[k.key_src[col][0]][k.key_src[col][1]];
+      }
+      inherit(lo, hi);
+    }
+  } else {
+    nc.ptr = r.agg.result + col;
+    nc.n_rows = 1;
+  }
+  const int32_t h = c->next++;
+  c->cols[h] = nc;
+  *out = h;
+  return PV_OK;
+}
+
 pv_status pv_column_stats(pv_ctx* c, pv_col h, int64_t* mn, int64_t* mx) {
   if (!c || !mn || !mx) return PV_ERR_INVALID_ARG;
   return column_stats(c, h, mn, mx);
@@ -782,12 +908,14 @@ pv_status pv_build_hash_table(pv_ctx* c, const pv_build_spec* spec, const pv_ht_
   if (!key) return fail(c, PV_ERR_INVALID_ARG, "unknown key column");
   if (key->type == PV_I64) return fail(c, PV_ERR_UNSUPPORTED, "int64 build keys");
   in.n_rows = key->n_rows;
+  in.n_dyn = key->n_dyn;
   in.key = key->ptr;
   in.key_type = key->type;
   in.n_preds = spec->n_preds;
   for (int i = 0; i < spec->n_preds; ++i) {
     const Column* pc = get(spec->preds[i].col);
-    if (!pc || pc->n_rows != key->n_rows) return fail(c, PV_ERR_INVALID_ARG, "bad build predicate column");
+    if (!pc || pc->n_rows != key->n_rows || pc->n_dyn != key->n_dyn)
+      return fail(c, PV_ERR_INVALID_ARG, "bad build predicate column");
     int64_t lo, hi;
     if (!pred_range(spec->preds[i], lo, hi)) return fail(c, PV_ERR_INVALID_ARG, "bad predicate op");
     in.pred_col[i] = pc->ptr;
@@ -798,7 +926,8 @@ pv_status pv_build_hash_table(pv_ctx* c, const pv_build_spec* spec, const pv_ht_
   in.n_payload = spec->n_payload;
   for (int i = 0; i < spec->n_payload; ++i) {
     const Column* pc = get(spec->payload[i]);
-    if (!pc || pc->n_rows != key->n_rows) return fail(c, PV_ERR_INVALID_ARG, "bad payload column");
+    if (!pc || pc->n_rows != key->n_rows || pc->n_dyn != key->n_dyn)
+      return fail(c, PV_ERR_INVALID_ARG, "bad payload column");
     if (pc->type == PV_I64) return fail(c, PV_ERR_UNSUPPORTED, "int64 payloads");
     in.pay_col[i] = pc->ptr;
     in.pay_type[i] = pc->type;
@@ -841,9 +970,10 @@ pv_status pv_run_pipeline(pv_ctx* c, const pv_pipeline_spec* spec, const pv_vari
   auto r = std::make_unique<Result>();
   pv_status s = canonicalize(c, spec, r->canon);
   if (s != PV_OK) return s;
+  if (var->interp != 0 && var->interp != 1) return fail(c, PV_ERR_INVALID_ARG, "interp must be 0 or 1");
   r->entry = find_shape(r->canon.sig);
-  if (!r->entry || r->entry->mode != r->canon.mode)
-    return fail(c, PV_ERR_UNSUPPORTED, "no compiled pipeline shape " + r->canon.sig);
+  if (r->entry && r->entry->mode != r->canon.mode) r->entry = nullptr;
+  r->generic = var->interp == 1 || r->canon.generic_only || r->entry == nullptr;
   r->var = *var;
   LaunchCfg L{};
   s = resolve_launch(c, r->var, L);
@@ -982,6 +1112,20 @@ pv_status pv_fetch_results(pv_ctx* c, pv_res h, int32_t n_cols, void* const* dst
   return PV_OK;
 }
 
+pv_status pv_result_kernel(pv_ctx* c, pv_res h, int32_t* generic, char* buf, int64_t cap) {
+  if (!c || !generic) return PV_ERR_INVALID_ARG;
+  auto it = c->results.find(h);
+  if (it == c->results.end()) return fail(c, PV_ERR_INVALID_ARG, "unknown result handle");
+  *generic = it->second->generic ? 1 : 0;
+  if (buf && cap > 0) {
+    const std::string& sig = it->second->canon.sig;
+    const size_t n = std::min<size_t>(sig.size(), static_cast<size_t>(cap - 1));
+    std::memcpy(buf, sig.data(), n);
+    buf[n] = 0;
+  }
+  return PV_OK;
+}
+
 pv_status pv_free(pv_ctx* c, int32_t h) {
   if (!c) return PV_ERR_INVALID_ARG;
   if (c->capturing) return fail(c, PV_ERR_INVALID_ARG, "cannot free while capturing");
@@ -998,6 +1142,8 @@ pv_status pv_free(pv_ctx* c, int32_t h) {
     cudaStreamSynchronize(c->stream);
     for (void* p : r->second->mem) dfree(c, p);
     c->results.erase(r);
+    for (auto it = c->cols.begin(); it != c->cols.end();)  // columns registered from the result
+      it = it->second.src_res == h ? c->cols.erase(it) : std::next(it);
     return PV_OK;
   }
   auto g = c->graphs.find(h);

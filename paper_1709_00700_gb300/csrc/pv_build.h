@@ -11,7 +11,8 @@
 namespace pv {
 
 struct BuildInput {
-  int64_t n_rows;
+  int64_t n_rows;                 // rows of the build table (an upper bound when n_dyn is set)
+  const unsigned long long* n_dyn; // row count read on the device (an earlier pipeline's result), or null
   const void* key;
   int key_type;
   int n_preds;
@@ -28,12 +29,15 @@ struct BuildParams {
   DevHT ht;
   int max_evictions;
   int32_t* err;
-  unsigned long long* pay_stats;  // [2]: max code, min code of the payload
+  unsigned long long* pay_stats;  // [2 * PV_MAX_PAYLOAD]: max code, min code of each payload column
 };
 
 struct BuildTable {
   DevHT ht{};
   int n_payload = 0;
+  bool indexed = false;               // two or more payload columns: slots hold the build row
+  const void* pay_col[PV_MAX_PAYLOAD]{};  // indexed tables gather their payloads from these columns
+  int pay_type[PV_MAX_PAYLOAD]{};
   int64_t pay_min[PV_MAX_PAYLOAD]{};  // over the surviving rows (empty: min > max)
   int64_t pay_max[PV_MAX_PAYLOAD]{};
   void* mem = nullptr;

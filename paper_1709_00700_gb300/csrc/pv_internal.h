@@ -85,6 +85,9 @@ struct ProjOut {
 struct GroupDesc {
   int n_keys;
   int n_aggs;
+  int coded;                     // keys are mixed-radix codes over the part domains (three parts, or two
+                                 // parts one of which is 64 bits wide); else packed (one part, or two
+                                 // 32-bit halves)
   int count_word;                // slot word holding the group's row count: the first
                                  // COUNT aggregate, else word n_aggs (hidden count)
   int32_t func[PV_MAX_AGGS];
@@ -125,6 +128,44 @@ struct GroupOut {
   unsigned long long* out_count;
 };
 
+// A pipeline program as data, for the generic (interpreted) kernels of
+// k_generic.cu: the same canonical slots, predicate ranges (KParams lo/hi)
+// and probes as the compiled shapes, with the key parts, aggregate terms and
+// projected values read from these tables at run time instead of being
+// compiled in.
+struct GRef {
+  int32_t kind;  // PV_REF_COL: fact slot a; PV_REF_PAYLOAD: payload b of probe a
+  int32_t a, b;
+};
+struct GTerm {
+  int32_t kind;  // pv_term_kind
+  GRef x;
+  int64_t c;
+};
+struct GAgg {
+  int32_t func;  // pv_func
+  int32_t n_terms;
+  GTerm t[PV_MAX_TERMS];
+};
+struct GenSpec {
+  int32_t n_slots, n_preds, n_probes, n_keys, n_aggs, n_proj;
+  int32_t slot_type[kMaxSlots];
+  int32_t pred_slot[PV_MAX_PREDS];   // predicate i: kp.lo[i] <= slot value <= kp.hi[i]
+  int32_t probe_slot[PV_MAX_PROBES]; // probe j: key column slot, table kp.probe[j]
+  GRef key[PV_MAX_KEYS];
+  GAgg agg[PV_MAX_AGGS];
+  GRef proj[PV_MAX_PROJ];
+  int32_t proj_type[PV_MAX_PROJ];
+  // Probed tables with several payload columns hold the build row in their
+  // slots; payload b of probe j is then gathered from pay_col[j][b].
+  int32_t indexed[PV_MAX_PROBES];
+  const void* pay_col[PV_MAX_PROBES][PV_MAX_PAYLOAD];
+  int32_t pay_type[PV_MAX_PROBES][PV_MAX_PAYLOAD];
+  // Row count read on the device when the kernel starts (the fact columns are
+  // the result of an earlier pipeline), at most KParams::n_rows; null: n_rows.
+  const unsigned long long* n_dyn;
+};
+
 struct ShapeEntry {
   std::string sig;
   int mode;
@@ -139,6 +180,17 @@ void register_shape(const ShapeEntry& e);
 const ShapeEntry* find_shape(const std::string& sig);
 void register_scan_shapes();
 void register_group_shapes();
+
+// Generic kernels (k_generic.cu): any pipeline program within the limits of
+// pv.h, with the program read from a GenSpec.  Return PV_ERR_UNSUPPORTED for
+// the variant axes they do not implement.
+pv_status generic_aggregate(const LaunchCfg& c, const KParams& kp, const GenSpec& gs, const AggOut& out);
+pv_status generic_project(const LaunchCfg& c, const KParams& kp, const GenSpec& gs, const ProjOut& out, int exec);
+pv_status generic_grouped(const LaunchCfg& c, const KParams& kp, const GenSpec& gs, const GroupDesc& gd,
+                          const GroupOut& g, const pv_variant& v);
+// Exclusive scan of the multi-pass tile counts (k_scan.cu), launched behind
+// the count kernel.
+pv_status launch_tile_scan(const LaunchCfg& c, const ProjOut& out, int32_t* err);
 
 // Cost-model kernels (k_mlp.cu).
 pv_status mlp_forward(cudaStream_t s, int* launches, const float* params, const float* x, const float* mu,

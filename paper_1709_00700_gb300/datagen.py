@@ -288,6 +288,38 @@ def star3_schema(n: int = 60_000_000, seed: int = DEFAULT_SEED) -> dict:
     return {"fact": star3_fact(n, seed), **{name: star3_dimension(name, seed) for name, _ in STAR3_DIMS}}
 
 
+# Order-processing schema shaped like TPC-H's, for the multi-pipeline query
+# (Section 9.2.1 runs TPC-H Q5, a chain of joins): 25 nations in 5 regions
+# (region = nation // 5); customers, orders and line items in TPC-H's
+# proportions (per scale factor 150,000 customers, 1,500,000 orders and about
+# 6,000,000 line items); dense keys stored in a shuffled order; foreign keys
+# uniform over the referenced keys; order dates uniform over 2,406 days from
+# DAY0 (1992-01-01 .. 1998-08-02 in TPC-H); extended price int64 fixed point
+# uniform [100, 1e7), discount uniform [0, 10] percent.
+TPCH_DAYS = 2406
+
+
+def tpch_schema(n_lineitem: int, seed: int = DEFAULT_SEED) -> dict:
+    n_orders = max(1, n_lineitem // 4)
+    n_cust = max(1, n_lineitem // 40)
+
+    def shuffled_keys(rows):
+        r = np.arange(rows, dtype=np.int64)
+        return ((r * coprime_multiplier(rows, 7919) + 17) % rows).astype(np.int32)
+
+    nation = np.arange(25, dtype=np.int32)
+    return {
+        "nation": {"n_nationkey": nation, "n_regionkey": (nation // 5).astype(np.int32)},
+        "customer": {"c_custkey": shuffled_keys(n_cust), "c_nationkey": uniform_int(seed, 801, n_cust, 0, 25, np.int32)},
+        "orders": {"o_orderkey": shuffled_keys(n_orders),
+                   "o_custkey": uniform_int(seed, 811, n_orders, 0, n_cust, np.int32),
+                   "o_orderdate": uniform_int(seed, 812, n_orders, DAY0, DAY0 + TPCH_DAYS, np.int32)},
+        "lineitem": {"l_orderkey": uniform_int(seed, 821, n_lineitem, 0, n_orders, np.int32),
+                     "l_extendedprice": uniform_int(seed, 822, n_lineitem, 100, 10_000_000, np.int64),
+                     "l_discount": uniform_int(seed, 823, n_lineitem, 0, 11, np.int64)},
+    }
+
+
 # ---------------------------------------------------------------------------
 # The same streams computed with torch (on any device), bit-identical to the
 # numpy definitions above.  uint64 arithmetic is carried in int64 tensors:

@@ -23,7 +23,7 @@ STATUS = {0: "PV_OK", -1: "PV_ERR_INVALID_ARG", -2: "PV_ERR_UNSUPPORTED", -3: "P
           -4: "PV_ERR_CUCKOO_CYCLE", -5: "PV_ERR_KEY_OUT_OF_RANGE", -6: "PV_ERR_DUP_BUILD_KEY",
           -7: "PV_ERR_OUTPUT_OVERFLOW", -8: "PV_ERR_TIMEOUT", -9: "PV_ERR_CUDA", -10: "PV_ERR_OOM"}
 PV_I32, PV_I64, PV_U8 = 0, 1, 2
-MAX_PREDS, MAX_PROBES, MAX_KEYS, MAX_AGGS, MAX_TERMS, MAX_PROJ, MAX_PAYLOAD = 4, 4, 3, 8, 3, 4, 1
+MAX_PREDS, MAX_PROBES, MAX_KEYS, MAX_AGGS, MAX_TERMS, MAX_PROJ, MAX_PAYLOAD = 4, 4, 3, 8, 3, 4, 4
 OPS = {"lt": 0, "le": 1, "gt": 2, "ge": 3, "eq": 4, "between": 5}
 FUNCS = {"sum": 0, "count": 1, "min": 2, "max": 3}
 TERMS = {"x": 0, "x_plus_c": 1, "c_minus_x": 2}
@@ -82,7 +82,7 @@ class pv_variant(ctypes.Structure):
                 ("block", ctypes.c_int32), ("grid_mult", ctypes.c_int32),
                 ("items_per_thread", ctypes.c_int32), ("threads_per_table", ctypes.c_int32),
                 ("cuckoo_k", ctypes.c_int32), ("prefetch", ctypes.c_int32), ("warp_agg", ctypes.c_int32),
-                ("seed", ctypes.c_uint64)]
+                ("interp", ctypes.c_int32), ("seed", ctypes.c_uint64)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -108,6 +108,10 @@ _SIGS = {
     "pv_fetch_result": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                          ctypes.c_int64, ctypes.c_int32]),
     "pv_free": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
+    "pv_result_kernel": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, _P(ctypes.c_int32), ctypes.c_char_p,
+                                          ctypes.c_int64]),
+    "pv_register_result_column": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_char_p,
+                                                   ctypes.c_char_p, _P(ctypes.c_int32)]),
     "pv_graph_capture_begin": (ctypes.c_int32, [ctypes.c_void_p]),
     "pv_graph_capture_end": (ctypes.c_int32, [ctypes.c_void_p, _P(ctypes.c_int32)]),
     "pv_graph_launch": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
@@ -170,10 +174,12 @@ class PVError(RuntimeError):
 
 def variant(exec="single", agg="local", pred="branch", access="grid", ht="linear", hash="murmur",
             block=256, grid_mult=0, items_per_thread=2, threads_per_table=0, cuckoo_k=3, seed=0,
-            prefetch=0, warp_agg=0) -> pv_variant:
-    """A pv_variant from readable names (the variant dimensions of Section 3.3)."""
+            prefetch=0, warp_agg=0, interp=0) -> pv_variant:
+    """A pv_variant from readable names (the variant dimensions of Section 3.3).
+    interp=1 runs the pipeline on the generic kernels even when a compiled
+    shape matches it."""
     return pv_variant(EXEC[exec], AGG[agg], PRED[pred], ACCESS[access], HT[ht], HASH[hash], block, grid_mult,
-                      items_per_thread, threads_per_table, cuckoo_k, prefetch, warp_agg, seed)
+                      items_per_thread, threads_per_table, cuckoo_k, prefetch, warp_agg, interp, seed)
 
 
 def ht_variant(kind="linear", hash="murmur", cuckoo_k=3, max_evictions=0, load_factor=0.5, seed=0) -> pv_ht_variant:
@@ -458,6 +464,19 @@ class Context:
             self.keep[(table, name)] = t
         return self
 
+    def register_result(self, res: int, table: str, names) -> "Context":
+        """Registers the columns of pipeline result `res` as table `table`
+        (pv_register_result_column): names[i] for result column i.  A later
+        pipeline or build over them reads what the producing pipeline wrote,
+        on the device, also when the whole chain is replayed as a graph."""
+        for i, name in enumerate(names):
+            h = ctypes.c_int32()
+            self._check(self.lib.pv_register_result_column(self.h, res, i, table.encode(), name.encode(),
+                                                           ctypes.byref(h)))
+            self.cols[(table, name)] = h.value
+            self.keep.pop((table, name), None)
+        return self
+
     def column_stats(self, table: str, name: str):
         lo, hi = ctypes.c_int64(), ctypes.c_int64()
         self._check(self.lib.pv_column_stats(self.h, self.cols[(table, name)], ctypes.byref(lo), ctypes.byref(hi)))
@@ -559,6 +578,30 @@ class Context:
     def free(self, handle: int):
         self._check(self.lib.pv_free(self.h, handle))
 
+    def result_kernel(self, res: int) -> tuple:
+        """(runs on the generic kernels, canonical shape signature) of a result."""
+        g = ctypes.c_int32()
+        buf = ctypes.create_string_buffer(1024)
+        self._check(self.lib.pv_result_kernel(self.h, res, ctypes.byref(g), buf, len(buf)))
+        return bool(g.value), buf.value.decode()
+
+    def run_chain(self, chain: list, variants: dict | None = None, htv: pv_ht_variant | None = None) -> "Chain":
+        """Runs a query of several pipelines (workloads.q5_chain format): for
+        each step in order, its build pipelines (over registered tables or
+        earlier steps' results), then its probe pipeline, whose result columns
+        are registered as table step["name"] (pv_register_result_column).
+        variants maps a step name to its pv_variant (default: variant()).
+        Returns a Chain whose rerun() enqueues every build and pipeline again,
+        allocation-free, so the whole query can be captured as one graph."""
+        steps = []
+        for st in chain:
+            hts = self.build_all(st["plan"], htv or ht_variant())
+            res = self.run(st["plan"], (variants or {}).get(st["name"], variant()), hts)
+            self.register_result(res, st["name"], st["columns"])
+            steps.append((st["name"], hts, res))
+        return Chain(self, steps)
+
+
     def query(self, plan: dict, var: pv_variant, htv: pv_ht_variant | None = None, keep: bool = False,
               probe_order=None):
         """Builds, runs and fetches a whole plan; returns int64 result columns
@@ -586,3 +629,49 @@ class Context:
             order = np.lexsort(tuple(cols[i] for i in reversed(range(nk))))
             cols = [c[order] for c in cols]
         return cols
+
+
+class Chain:
+    """The table and result handles of a multi-pipeline query run by
+    Context.run_chain."""
+
+    def __init__(self, ctx: Context, steps: list):
+        self.ctx, self.steps = ctx, steps
+        self.graph = None
+
+    def rerun(self):
+        """Enqueues every step again: its builds (pv_rebuild_hash_table), then
+        its pipeline (pv_rerun).  No allocation, no synchronisation."""
+        for _, hts, res in self.steps:
+            for h in hts:
+                self.ctx.rebuild(h)
+            self.ctx.rerun(res)
+
+    def capture(self) -> int:
+        """Records rerun() as one CUDA graph (pv_graph_capture_*); returns its handle."""
+        ctx = self.ctx
+        ctx._check(ctx.lib.pv_graph_capture_begin(ctx.h))
+        try:
+            self.rerun()
+        finally:
+            g = ctypes.c_int32()
+            ctx._check(ctx.lib.pv_graph_capture_end(ctx.h, ctypes.byref(g)))
+        self.graph = g.value
+        return self.graph
+
+    def launch(self):
+        self.ctx._check(self.ctx.lib.pv_graph_launch(self.ctx.h, self.graph))
+
+    def fetch(self, step: int = -1) -> list:
+        """Result columns of a step (the last by default), as produced."""
+        return self.ctx.fetch(self.steps[step][2])
+
+    def free(self):
+        if self.graph is not None:
+            self.ctx.free(self.graph)
+            self.graph = None
+        for _, hts, res in reversed(self.steps):
+            self.ctx.free(res)
+            for h in hts:
+                self.ctx.free(h)
+        self.steps = []

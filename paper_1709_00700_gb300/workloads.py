@@ -105,3 +105,42 @@ def star3_plan(regions=STAR3_REGIONS, years=STAR3_YEARS) -> dict:
 def parts_text_plan(filters=(("category", "eq", "MFGR#12"), ("brand", "between", "MFGR#1221", "MFGR#1228"))) -> dict:
     return {"fact": "parts", "filters": [list(f) for f in filters],
             "aggs": [["sum", [["x", "price"]]], ["count"]]}
+
+
+# A query of several pipelines where later pipelines read earlier results,
+# shaped like TPC-H Q5 (Section 9.2.1): revenue of the line items whose order
+# falls in one year and whose customer lives in a nation of the first
+# `regions` regions, per nation, then per region.  Each step is a pipeline
+# program; its result columns become table step["name"] with step["columns"],
+# which later steps build hash tables on (a build over a probe pipeline's
+# result) or scan (an aggregation over an aggregation):
+#   cust:   customers of the selected nations        (probe, PROJECT)
+#   ord:    orders of the year by those customers    (build on cust, probe, PROJECT)
+#   nat:    line items of those orders, per nation   (build on ord, probe, HASH_AGGREGATE)
+#   region: the nations' revenue per region          (probe, HASH_AGGREGATE over nat)
+Q5_YEAR = (datagen.DAY0 + 730, datagen.DAY0 + 1094)   # the third year of the order dates
+
+
+def q5_chain(regions: int = 3, days=Q5_YEAR) -> list:
+    sel_nations = {"table": "nation", "key": "n_nationkey", "filters": [["n_regionkey", "lt", regions]],
+                   "payload": []}
+    return [
+        {"name": "cust", "columns": ["custkey", "nation"],
+         "plan": {"fact": "customer", "builds": [sel_nations], "probes": [{"build": 0, "fk": "c_nationkey"}],
+                  "project": ["c_custkey", "c_nationkey"]}},
+        {"name": "ord", "columns": ["orderkey", "nation"],
+         "plan": {"fact": "orders", "filters": [["o_orderdate", "between", days[0], days[1]]],
+                  "builds": [{"table": "cust", "key": "custkey", "filters": [], "payload": ["nation"]}],
+                  "probes": [{"build": 0, "fk": "o_custkey"}], "project": ["o_orderkey", ["payload", 0, 0]]}},
+        {"name": "nat", "columns": ["nation", "revenue", "lines"],
+         "plan": {"fact": "lineitem",
+                  "builds": [{"table": "ord", "key": "orderkey", "filters": [], "payload": ["nation"]}],
+                  "probes": [{"build": 0, "fk": "l_orderkey"}], "group_by": [["payload", 0, 0]],
+                  "aggs": [["sum", [["x", "l_extendedprice"], ["c_minus_x", "l_discount", 100]]], ["count"]]}},
+        {"name": "region", "columns": ["region", "revenue", "lines", "nations", "top_nation_revenue"],
+         "plan": {"fact": "nat",
+                  "builds": [{"table": "nation", "key": "n_nationkey", "filters": [], "payload": ["n_regionkey"]}],
+                  "probes": [{"build": 0, "fk": "nation"}], "group_by": [["payload", 0, 0]],
+                  "aggs": [["sum", [["x", "revenue"]]], ["sum", [["x", "lines"]]], ["count"],
+                           ["max", [["x", "revenue"]]]]}},
+    ]
