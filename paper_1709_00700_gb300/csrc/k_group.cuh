@@ -444,15 +444,62 @@ struct SinkClusterPerfect {
   }
 };
 
+// Word layout of a thread-private slot.  Wide: word a holds aggregate a
+// (SUM/COUNT raw, MIN/MAX as codes), then the row count unless a COUNT
+// aggregate already counts rows.  NARROW: the narrow aggregates (NarrowAgg:
+// SUM of a plain column, COUNT) and the hidden row count are 32-bit fields,
+// two to a word (field f in word f / 2, half f % 2), then one word per other
+// aggregate.  Both are padded to an even number of words.
+struct SlotLayout {
+  int word[PV_MAX_AGGS + 1];  // word of aggregate a (index NA: the hidden row count)
+  int half[PV_MAX_AGGS + 1];  // 0 / 1: low / high 32-bit field; -1: the whole word
+  int agg[2 * PV_MAX_AGGS + 2][2];  // per word, the aggregate of each field (-1: none); wide words use [0]
+  int narrow_words;           // words holding 32-bit fields (they come first)
+  int sw;                     // words per slot (even)
+};
+
+template <class A, bool NARROW>
+constexpr SlotLayout make_slot_layout(int na, int ca) {
+  SlotLayout L{};
+  for (int w = 0; w < 2 * PV_MAX_AGGS + 2; ++w) L.agg[w][0] = L.agg[w][1] = -1;
+  const int count_hidden = ca < 0;
+  int f = 0;
+  if (NARROW) {
+    for (int a = 0; a <= na; ++a) {
+      const bool narrow = a < na ? A::narrow_of[a < na ? a : 0] : count_hidden;
+      if (!narrow) continue;
+      L.word[a] = f / 2;
+      L.half[a] = f % 2;
+      L.agg[f / 2][f % 2] = a;
+      ++f;
+    }
+  }
+  L.narrow_words = (f + 1) / 2;
+  int w = L.narrow_words;
+  for (int a = 0; a <= na; ++a) {
+    const bool narrow = NARROW && (a < na ? A::narrow_of[a < na ? a : 0] : count_hidden);
+    if (narrow || (a == na && !count_hidden)) continue;
+    L.word[a] = w;
+    L.half[a] = -1;
+    L.agg[w][0] = a;
+    ++w;
+  }
+  L.sw = (w + 1) & ~1;
+  return L;
+}
+
 // Thread-private perfect arrays (M = 1): no atomics until the CTA epilogue.
-// A slot holds SW words (the aggregates, the row count unless a COUNT
-// aggregate already counts rows, padded to an even count) stored as SW / 2
-// 16-byte pairs, interleaved by thread: pair j of slot s of thread t is at
-// 16-byte unit (s * SW / 2 + j) * blockDim + t, so the 8 lanes of a memory
-// phase always touch 8 distinct bank groups, whatever slot each lane updates.
-// Slot cap is a scratch slot: a dead row (software predication) updates it
-// instead of masking every value.
-template <class SH>
+// A slot holds SW words (SlotLayout) stored as SW / 2 16-byte pairs,
+// interleaved by thread: pair j of slot s of thread t is at 16-byte unit
+// (s * SW / 2 + j) * blockDim + t, so the 8 lanes of a memory phase always
+// touch 8 distinct bank groups, whatever slot each lane updates.  Dead rows
+// skip the update.  With NARROW, the 32-bit fields hold a thread's partial
+// sums of the narrow aggregates: a row updates them only when each of its
+// narrow values is at most g.narrow_limit = (2^32 - 1) / (rows the thread
+// visits), so no field can overflow; any other row adds its codes straight
+// into the global table.  Fewer words per slot mean less shared-memory
+// traffic per row, the limit of this sink.
+template <class SH, bool NARROW = false>
 struct SinkThreadPerfect {
   // Tables of 256 threads x (cap x 16 B units) let three CTAs share an SM;
   // the predicated loop then runs without register double buffering.
@@ -461,16 +508,19 @@ struct SinkThreadPerfect {
   using A = typename SH::Aggs;
   static constexpr int NA = A::N;
   static constexpr int CA = count_index<A>();
-  static constexpr int SW = ((CA >= 0 ? NA : NA + 1) + 1) & ~1;
+  static constexpr SlotLayout L = make_slot_layout<A, NARROW>(NA, CA);
+  static constexpr int SW = L.sw;
   static constexpr int SP = SW / 2;
+  static constexpr int NW = L.narrow_words;
   static __host__ __device__ int64_t units_per_thread(int64_t cap) { return cap * SP; }
   static __host__ __device__ size_t smem_bytes(int64_t cap, int block) {
     return static_cast<size_t>(units_per_thread(cap)) * 16 * block;
   }
   template <int W>
   static __device__ __forceinline__ constexpr int word_func() {
-    if constexpr (W < NA) return A::func_of[W];
-    else return PV_SUM;
+    constexpr int ag = L.agg[W][0];
+    if constexpr (W < NW || ag < 0 || ag >= NA) return PV_SUM;
+    else return A::func_of[ag < NA && ag >= 0 ? ag : 0];
   }
   const GroupDesc& gd; const GroupOut& g; int32_t* err; ulonglong2* sm;
   uint32_t sbase;        // shared address of this thread's unit 0 of slot 0
@@ -489,17 +539,36 @@ struct SinkThreadPerfect {
     bad |= !ok && live;
     if (!(ok && live)) return;
     uint64_t v[SW];
-    static_for<SW>([&](auto w) {
-      constexpr int I = decltype(w)::value;
-      if constexpr (I < NA) {
-        using AG = typename At<(I < NA ? I : 0), typename A::L>::type;
-        v[I] = acc_code<AG::func>(agg_value<AG>(it, kp, r));
+#pragma unroll
+    for (int j = 0; j < SW; ++j) v[j] = 0;
+    bool fits = true;  // every narrow value within the limit
+    static_for<NA>([&](auto a) {
+      constexpr int I = decltype(a)::value;
+      using AG = typename At<I, typename A::L>::type;
+      constexpr int WI = L.word[I], HI = L.half[I];
+      const int64_t x = agg_value<AG>(it, kp, r);
+      if constexpr (HI >= 0) {
+        fits = fits && static_cast<uint64_t>(x) <= g.narrow_limit;
+        v[WI] += static_cast<uint64_t>(static_cast<uint32_t>(x)) << (32 * HI);
       } else {
-        v[I] = (CA < 0 && I == NA) ? 1ull : 0ull;
+        v[WI] = acc_code<AG::func>(x);
       }
     });
+    if constexpr (CA < 0) {
+      constexpr int WC = L.word[NA], HC = L.half[NA];
+      v[WC] += HC >= 0 ? (1ull << (32 * HC)) : 1ull;
+    }
+    if constexpr (NARROW) {
+      if (!fits) {  // a value too large for the 32-bit fields: straight to the global table
+        uint64_t c[NA + 1];
+        row_codes<SH>(it, kp, r, ~0ull, c);
+        slot_atomic_add<SH>(g.vals + (blockIdx.x % g.replicas) * g.rep_stride + s * g.stride, c);
+        return;
+      }
+    }
     // unit J of slot s: sbase + (s * SP + J) * ustride; volatile asm keeps
-    // each read-modify-write in program order (rows may share a slot)
+    // each read-modify-write in program order (rows may share a slot).  A
+    // narrow word adds both of its fields at once: they cannot carry.
     const uint32_t a = sbase + static_cast<uint32_t>(s) * (SP * ustride);
     const uint32_t us = ustride;
     unsigned long long w[SW];
@@ -515,33 +584,59 @@ struct SinkThreadPerfect {
       asm volatile("st.shared.v2.u64 [%0], {%1, %2};" ::"r"(a + J * us), "l"(x), "l"(y) : "memory");
     });
   }
+  // CTA epilogue: one warp per (slot, word) folds the word over the CTA's
+  // threads (32-bit fields summed as 64-bit values) and adds the result into
+  // the aggregate's word of the global table.
   __device__ void finish() {
     if (bad) set_error(err, PV_ERR_KEY_OUT_OF_RANGE);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const unsigned long long* w64 = reinterpret_cast<const unsigned long long*>(sm);
-    constexpr int used = CA >= 0 ? NA : NA + 1;
+    int agg0[SW], agg1[SW];  // aggregate of each word's fields
+    static_for<SW>([&](auto jj) {
+      constexpr int J = decltype(jj)::value;
+      constexpr int a0 = L.agg[J][0], a1 = L.agg[J][1];
+      agg0[J] = a0;
+      agg1[J] = a1;
+    });
     for (int64_t w = warp; w < g.cap * SW; w += nwarps) {
       const int64_t slot = w / SW;
-      const int a = static_cast<int>(w % SW);
-      if (a >= used) continue;
-      const bool add = a >= NA || gd.func[a] == PV_SUM || gd.func[a] == PV_COUNT;
-      const int64_t unit = slot * SP + a / 2;
+      const int j = static_cast<int>(w % SW);
+      const int64_t unit = slot * SP + j / 2;
+      unsigned long long* dst = g.vals + (blockIdx.x % g.replicas) * g.rep_stride + slot * g.stride;
+      if (j < NW) {
+        uint64_t lo = 0, hi = 0;
+        for (int t = lane; t < static_cast<int>(blockDim.x); t += 32) {
+          const uint64_t x = w64[2 * (unit * blockDim.x + t) + (j & 1)];
+          lo += x & 0xffffffffull;
+          hi += x >> 32;
+        }
+        lo = warp_reduce<PV_SUM>(lo);
+        hi = warp_reduce<PV_SUM>(hi);
+        if (lane == 0) {
+          if (lo && agg0[j] >= 0) atomicAdd(dst + agg0[j], static_cast<unsigned long long>(lo));
+          if (hi && agg1[j] >= 0) atomicAdd(dst + agg1[j], static_cast<unsigned long long>(hi));
+        }
+        continue;
+      }
+      const int ag = agg0[j];
+      if (ag < 0) continue;  // padding
+      const bool add = ag >= NA || gd.func[ag] == PV_SUM || gd.func[ag] == PV_COUNT;
       uint64_t v = 0;
       for (int t = lane; t < static_cast<int>(blockDim.x); t += 32) {
-        const uint64_t x = w64[2 * (unit * blockDim.x + t) + (a & 1)];
+        const uint64_t x = w64[2 * (unit * blockDim.x + t) + (j & 1)];
         v = add ? v + x : (x > v ? x : v);
       }
       v = add ? warp_reduce<PV_SUM>(v) : warp_reduce<PV_MAX>(v);
       if (lane == 0 && v) {
-        unsigned long long* dst = g.vals + (blockIdx.x % g.replicas) * g.rep_stride + slot * g.stride;
-        if (a == NA) atomicAdd(dst + NA, static_cast<unsigned long long>(v));  // row count word
-        else if (add) atomicAdd(dst + a, static_cast<unsigned long long>(v));
-        else atomicMax(dst + a, static_cast<unsigned long long>(v));
+        if (add) atomicAdd(dst + ag, static_cast<unsigned long long>(v));
+        else atomicMax(dst + ag, static_cast<unsigned long long>(v));
       }
     }
   }
 };
+template <class SH> using SinkThreadPerfectW = SinkThreadPerfect<SH, false>;
+template <class SH> using SinkThreadPerfectN = SinkThreadPerfect<SH, true>;
 
 // CTA-local linear-probing table in shared memory; rows whose key does not
 // find a place within kLocalProbe steps go straight to the global table.
@@ -830,8 +925,13 @@ static pv_status launch_k(const LaunchCfg& c, K k, const KParams& kp, const Grou
   }
   const int grid = grid_for(c, reinterpret_cast<const void*>(k), smem, kp.n_items, static_cast<int64_t>(c.block) * U);
   if (grid <= 0) return PV_ERR_UNSUPPORTED;
+  // rows one thread visits, at most: its items (grid-stride or chunked) of 4 rows, or for compacted
+  // execution as many queued rows, plus one partial drain
+  const int64_t T = static_cast<int64_t>(grid) * c.block;
+  GroupOut g2 = g;
+  g2.narrow_limit = static_cast<uint64_t>(UINT32_MAX) / static_cast<uint64_t>(4 * ((kp.n_items + T - 1) / T) + 4);
   kmark(c);
-  k<<<grid, c.block, smem, c.stream>>>(kp, gd, g);
+  k<<<grid, c.block, smem, c.stream>>>(kp, gd, g2);
   kmark(c);
   ++*c.launches;
   return cudaGetLastError() == cudaSuccess ? PV_OK : PV_ERR_CUDA;
@@ -971,9 +1071,16 @@ static pv_status launch_group(const LaunchCfg& c, const KParams& kp, const Group
     if (!local) {
       s = run_group<SH, UMASK, SinkGlobalPerfect>(c, kp, gd, g, 0);
     } else if (v.threads_per_table == 1) {
-      const size_t smem = SinkThreadPerfect<SH>::smem_bytes(g.cap, c.block);
-      if (smem > 200 * 1024) return PV_ERR_UNSUPPORTED;
-      s = run_group<SH, UMASK, SinkThreadPerfect>(c, kp, gd, g, smem);
+      // 32-bit fields for the narrow aggregates when that saves words per slot
+      if constexpr (SinkThreadPerfectN<SH>::SW < SinkThreadPerfectW<SH>::SW) {
+        const size_t smem = SinkThreadPerfectN<SH>::smem_bytes(g.cap, c.block);
+        if (smem > 200 * 1024) return PV_ERR_UNSUPPORTED;
+        s = run_group<SH, UMASK, SinkThreadPerfectN>(c, kp, gd, g, smem);
+      } else {
+        const size_t smem = SinkThreadPerfectW<SH>::smem_bytes(g.cap, c.block);
+        if (smem > 200 * 1024) return PV_ERR_UNSUPPORTED;
+        s = run_group<SH, UMASK, SinkThreadPerfectW>(c, kp, gd, g, smem);
+      }
     } else {
       const size_t smem = static_cast<size_t>(g.cap) * slot_bytes;
       if (smem > kLocalPerfectBytes) return PV_ERR_UNSUPPORTED;

@@ -1187,6 +1187,7 @@ pv_status pv_graph_launch(pv_ctx* c, pv_graph h) {
   auto g = c->graphs.find(h);
   if (g == c->graphs.end()) return fail(c, PV_ERR_INVALID_ARG, "unknown graph handle");
   PV_CUDA(c, cudaGraphLaunch(g->second.exec, c->stream));
+  for (auto& kv : c->results) kv.second->rows_cached = -1;  // the replay may change any result's rows
   return PV_OK;
 }
 

@@ -225,11 +225,20 @@ template <class E> struct Max {
   static void sig(std::string& s) { s += "M"; E::sig(s); }
 };
 
+// Aggregates whose per-row value is one plain column value (SUM(x)) or 1
+// (COUNT): a thread's partial sum of them fits 32 bits whenever every value
+// it adds is at most (2^32 - 1) / rows the thread visits, so a thread-private
+// table may keep them as 32-bit fields, two to a 64-bit word.
+template <class A> struct NarrowAgg : std::false_type {};
+template <> struct NarrowAgg<Count> : std::true_type {};
+template <int S> struct NarrowAgg<Sum<Mul<X<S>>>> : std::true_type {};
+
 template <class... As> struct Aggs {
   static constexpr int N = sizeof...(As);
   static constexpr uint32_t slots = (0u | ... | As::slots);
   using L = TList<As...>;
   static constexpr int func_of[N > 0 ? N : 1] = {As::func...};
+  static constexpr bool narrow_of[N > 0 ? N : 1] = {NarrowAgg<As>::value...};
   static void sig(std::string& s) { s += "|A:"; ((As::sig(s), s += ","), ...); }
 };
 

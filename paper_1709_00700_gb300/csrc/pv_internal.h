@@ -122,6 +122,10 @@ struct GroupOut {
   int cluster_log2;   // cluster tables: log2 of the CTAs per cluster (the table's partitions)
   int replicas;       // 1 for hashed tables
   int64_t rep_stride; // words between replicas: (cap + 1) * stride
+  // Thread-private tables with 32-bit fields: a row whose field values are
+  // all at most narrow_limit = (2^32 - 1) / (rows a thread visits) updates its
+  // thread's table; any other row updates the global table directly.
+  uint64_t narrow_limit;
   // Extraction (dense result columns, int64): out[c * out_cap + row].
   int64_t* out;
   int64_t out_cap;

@@ -164,6 +164,29 @@ def test_lowcard_grouped_all_variants(ctx):
     _grouped_all_variants(ctx, workloads.lowcard_plan(), li, min_ran=60)
 
 
+@pytest.mark.parametrize("n,big", [(60_001, 0.001), (4_099, 0.3), (1_000_003, 0.00001)])
+def test_lowcard_thread_private_32bit_fields(ctx, n, big):
+    """Thread-private tables keep the plain-column sums and the count in 32-bit
+    fields; rows whose values could overflow a field (here: large and negative
+    quantities and prices, a fraction `big` of the rows) go straight to the
+    global table.  Both paths, exact against the oracle."""
+    li = datagen.table_lowcard_groups(n, seed=n)
+    rng = np.random.default_rng(n)
+    pick = rng.random(n) < big
+    li["qty"] = np.where(pick, rng.integers(-2**40, 2**40, n), li["qty"]).astype(np.int64)
+    pick = rng.random(n) < big
+    li["price"] = np.where(pick, rng.integers(2**31, 2**33, n), li["price"]).astype(np.int64)
+    t = {"li": li}
+    register(ctx, t)
+    w = want(workloads.lowcard_plan(), t)
+    for kw in (dict(pred="predicated"), dict(pred="branch"), dict(pred="compacted"),
+               dict(pred="predicated", block=1024, grid_mult=1), dict(pred="branch", prefetch=1, block=64)):
+        kw = dict(kw, agg="local", ht="perfect", threads_per_table=1, items_per_thread=1)
+        got = run_or_skip(ctx, workloads.lowcard_plan(), pv.variant(**kw))
+        if got is not None:
+            assert_same(got, w, ctxmsg=str(kw))
+
+
 @pytest.mark.parametrize("g,dist", [(1, "uniform"), (10, "zipf"), (1000, "uniform"), (1000, "zipf"),
                                     (50_000, "uniform")])
 def test_keyval_grouped_all_variants(ctx, g, dist):
