@@ -861,18 +861,22 @@ __global__ void __maxnreg__((GroupRegs<SH, Sink, PRED>::value)) k_group(const __
 // Compacted execution of a grouped pipeline: for_rows_compacted queues the
 // survivors of the first operation per warp; each queued row runs the other
 // probes, the sink's column loads and the sink, one row per lane.
-template <class SH, class Sink>
+template <class SH, class Sink, int K>
 __global__ void __maxnreg__((GroupRegs<SH, Sink, false>::value)) k_group_compact(
     const __grid_constant__ KParams kp, const __grid_constant__ GroupDesc gd, const __grid_constant__ GroupOut g) {
   extern __shared__ unsigned long long smem[];
   const int nwarps = blockDim.x >> 5;
-  uint32_t* q = reinterpret_cast<uint32_t*>(smem) + (threadIdx.x >> 5) * kQueueCap;
+  uint32_t* q = reinterpret_cast<uint32_t*>(smem) + (threadIdx.x >> 5) * queue_cap<K>();
   if (blockIdx.x == 0 && threadIdx.x == 0) *g.out_count = 0;  // extraction runs after this kernel
-  Sink sink(gd, g, kp.err, smem + nwarps * kQueueCap / 2);     // 640 bytes of queue per warp
+  Sink sink(gd, g, kp.err, smem + nwarps * queue_cap<K>() / 2);  // the queues, 4 bytes an entry
   sink.init();
-  for_rows_compacted<SH>(kp, q, [&](uint32_t row) {
-    Item<SH> it;
-    if (compact_load_row<SH>(it, kp, row)) sink.add(it, kp, 0, true);
+  for_rows_compacted<SH, K>(kp, q, [&](const uint32_t (&rows)[K], const bool (&has)[K]) {
+    Item<SH> it[K];
+    bool ok[K];
+    compact_load_rows<SH, K>(it, ok, kp, rows, has);
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      if (ok[k]) sink.add(it[k], kp, 0, true);
   });
   pdl_launch_dependents();
   sink.finish();
@@ -943,9 +947,14 @@ static pv_status run_group_compact(const LaunchCfg& c, const KParams& kp, const 
   if constexpr (SH::Where::N == 0 && SH::Probes::N == 0) {
     return PV_ERR_UNSUPPORTED;  // nothing to compact on
   } else {
-    if (c.chunk || c.U != 1 || kp.n_rows > static_cast<int64_t>(UINT32_MAX)) return PV_ERR_UNSUPPORTED;
-    const size_t smem = static_cast<size_t>(c.block / 32) * kQueueCap * 4 + sink_smem;
-    return launch_k(c, k_group_compact<SH, SinkT<SH>>, kp, gd, g, smem, 1);
+    // items_per_thread: queued rows a lane takes through the row stage at once
+    if (c.chunk || (c.U != 1 && c.U != 2) || kp.n_rows > static_cast<int64_t>(UINT32_MAX)) return PV_ERR_UNSUPPORTED;
+    if (c.U == 2) {
+      const size_t smem = static_cast<size_t>(c.block / 32) * queue_cap<2>() * 4 + sink_smem;
+      return launch_k(c, k_group_compact<SH, SinkT<SH>, 2>, kp, gd, g, smem, 1);
+    }
+    const size_t smem = static_cast<size_t>(c.block / 32) * queue_cap<1>() * 4 + sink_smem;
+    return launch_k(c, k_group_compact<SH, SinkT<SH>, 1>, kp, gd, g, smem, 1);
   }
 }
 

@@ -338,7 +338,7 @@ __global__ void __maxnreg__(128) k_project_scatter(const __grid_constant__ KPara
 // ---------------------------------------------------------------------------
 // Compacted execution of an ungrouped aggregation: the rows that survive the
 // first operation are queued per warp and accumulated one per lane.
-template <class SH>
+template <class SH, int K>
 __global__ void __maxnreg__(128) k_aggregate_compact(const __grid_constant__ KParams kp,
                                                      const __grid_constant__ AggOut out) {
   using A = typename SH::Aggs;
@@ -347,17 +347,36 @@ __global__ void __maxnreg__(128) k_aggregate_compact(const __grid_constant__ KPa
   uint64_t acc[NA + 1];
 #pragma unroll
   for (int a = 0; a <= NA; ++a) acc[a] = 0;
-  for_rows_compacted<SH>(kp, qmem + (threadIdx.x >> 5) * kQueueCap, [&](uint32_t row) {
-    Item<SH> it;
-    if (!compact_load_row<SH>(it, kp, row)) return;
-    static_for<NA>([&](auto a) {
-      constexpr int I = decltype(a)::value;
-      using AG = typename At<I, typename A::L>::type;
-      acc[I] = acc_combine<AG::func>(acc[I], acc_code<AG::func>(agg_value<AG>(it, kp, 0)));
-    });
-    acc[NA] += 1;
+  for_rows_compacted<SH, K>(kp, qmem + (threadIdx.x >> 5) * queue_cap<K>(),
+                            [&](const uint32_t (&rows)[K], const bool (&has)[K]) {
+    Item<SH> it[K];
+    bool ok[K];
+    compact_load_rows<SH, K>(it, ok, kp, rows, has);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (!ok[k]) continue;
+      static_for<NA>([&](auto a) {
+        constexpr int I = decltype(a)::value;
+        using AG = typename At<I, typename A::L>::type;
+        acc[I] = acc_combine<AG::func>(acc[I], acc_code<AG::func>(agg_value<AG>(it[k], kp, 0)));
+      });
+      acc[NA] += 1;
+    }
   });
   aggregate_epilogue<SH>(acc, out);
+}
+
+template <class SH, int K>
+static pv_status launch_agg_compact_k(const LaunchCfg& c, const KParams& kp, const AggOut& out) {
+  auto k = k_aggregate_compact<SH, K>;
+  const size_t smem = static_cast<size_t>(c.block / 32) * queue_cap<K>() * 4;
+  const int grid = grid_for(c, reinterpret_cast<const void*>(k), smem, kp.n_items, c.block);
+  if (grid <= 0) return PV_ERR_UNSUPPORTED;
+  kmark(c);
+  k<<<grid, c.block, smem, c.stream>>>(kp, out);
+  kmark(c);
+  ++*c.launches;
+  return cudaGetLastError() == cudaSuccess ? PV_OK : PV_ERR_CUDA;
 }
 
 template <class SH>
@@ -365,16 +384,9 @@ static pv_status launch_agg_compact(const LaunchCfg& c, const KParams& kp, const
   if constexpr (SH::Where::N == 0 && SH::Probes::N == 0) {
     return PV_ERR_UNSUPPORTED;  // nothing to compact on
   } else {
-    if (c.chunk || c.U != 1 || kp.n_rows > static_cast<int64_t>(UINT32_MAX)) return PV_ERR_UNSUPPORTED;
-    auto k = k_aggregate_compact<SH>;
-    const size_t smem = static_cast<size_t>(c.block / 32) * kQueueCap * 4;
-    const int grid = grid_for(c, reinterpret_cast<const void*>(k), smem, kp.n_items, c.block);
-    if (grid <= 0) return PV_ERR_UNSUPPORTED;
-    kmark(c);
-    k<<<grid, c.block, smem, c.stream>>>(kp, out);
-    kmark(c);
-    ++*c.launches;
-    return cudaGetLastError() == cudaSuccess ? PV_OK : PV_ERR_CUDA;
+    // items_per_thread: queued rows a lane takes through the row stage at once
+    if (c.chunk || (c.U != 1 && c.U != 2) || kp.n_rows > static_cast<int64_t>(UINT32_MAX)) return PV_ERR_UNSUPPORTED;
+    return c.U == 2 ? launch_agg_compact_k<SH, 2>(c, kp, out) : launch_agg_compact_k<SH, 1>(c, kp, out);
   }
 }
 

@@ -312,13 +312,20 @@ __device__ __forceinline__ void for_items_pipelined(const KParams& kp, F&& consu
 // Compacted execution (variant pred = PV_COMPACTED).  The pipeline's first
 // operation (its filters, or else its first probe) runs over whole items as
 // in branched mode; the rows it keeps are appended to a queue per warp in
-// shared memory, and each 32 queued rows are taken one per lane through the
+// shared memory, and each 32 * K queued rows are taken K per lane through the
 // remaining operations (the probes, the loads of the sink's columns) and
-// the sink (a grouped table, or a thread's ungrouped accumulators).  After a selective first operation the later operations then
-// run on full warps, not on the few live lanes of every warp.  Queue
+// the sink (a grouped table, or a thread's ungrouped accumulators).  After a
+// selective first operation the later operations then run on full warps, not
+// on the few live lanes of every warp.  A lane takes its K rows through each
+// stage together, so their dependent loads (a key column, then the table, then
+// the next key column ...) are in flight together: K = 2 doubles the memory
+// requests a warp has outstanding (variant items_per_thread = 2).  Queue
 // entries are 32-bit row indices (tables of fewer than 2^32 rows).
 // ---------------------------------------------------------------------------
-constexpr int kQueueCap = 32 + 128;  // a drain leaves < 32 rows; one trip appends at most 32 lanes x 4 rows
+// Queue entries per warp: a drain leaves fewer than 32 * K rows, and one trip
+// appends at most 32 lanes x 4 rows.
+template <int K>
+__host__ __device__ constexpr int queue_cap() { return 32 * K + 128; }
 
 // Whether an expression tree (Key, Aggs, Proj and their terms) reads the
 // payload bound by probe J.
@@ -363,62 +370,83 @@ __device__ __forceinline__ void compact_first(Item<SH>& it, const KParams& kp, i
   }
 }
 
-// One queued row as item row 0: the probes (the first probe again when it
-// was the first operation and its payload is read), then the loads of the
-// columns the sink reads.  Returns false when a probe misses.
-template <class SH>
-__device__ __forceinline__ bool compact_load_row(Item<SH>& it, const KParams& kp, uint32_t row) {
+// K queued rows (has[k]: row k exists) as row 0 of K items: the probes stage
+// by stage for all K rows (the first probe again when it was the first
+// operation and its payload is read), then the loads of the columns the sink
+// reads.  ok[k] is false when a probe missed.
+template <class SH, int K>
+__device__ __forceinline__ void compact_load_rows(Item<SH> (&it)[K], bool (&ok)[K], const KParams& kp,
+                                                  const uint32_t (&row)[K], const bool (&has)[K]) {
   using JP = typename SH::Probes;
-  it.nvalid = 1;
-  it.mask = 1u;
-  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    it[k].nvalid = 1;
+    it[k].mask = 1u;
+    ok[k] = has[k];
+  }
   static_for<JP::N>([&](auto j) {
     constexpr int J = decltype(j)::value;
     constexpr int S = JP::slot_of[J];
     using T = typename At<S, typename SH::Cols::L>::type::T;
-    if (J == 0 && compact_skip_probe0<SH>()) {
-      it.pay[J][0] = 0;  // the first operation was this probe, and its payload is not read
-    } else if (ok) {
-      const T key = __ldg(static_cast<const T*>(kp.col[S]) + row);
-      VGet<S>::get(it.v)[0] = key;
-      int32_t p = 0;
-      ok = probe_key(kp.probe[J], static_cast<int64_t>(key), p);
-      it.pay[J][0] = p;
+    if constexpr (J == 0 && compact_skip_probe0<SH>()) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) it[k].pay[J][0] = 0;  // the first operation was this probe, payload unread
+    } else {
+      T key[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) key[k] = ok[k] ? __ldg(static_cast<const T*>(kp.col[S]) + row[k]) : T(0);
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        VGet<S>::get(it[k].v)[0] = key[k];
+        int32_t p = 0;
+        if (ok[k]) ok[k] = probe_key(kp.probe[J], static_cast<int64_t>(key[k]), p);
+        it[k].pay[J][0] = p;
+      }
     }
   });
-  if (!ok) return false;
   static_for<SH::Cols::N>([&](auto c) {
     constexpr int S = decltype(c)::value;
     if constexpr ((compact_row_slots<SH>() >> S) & 1u) {
       using T = typename At<S, typename SH::Cols::L>::type::T;
-      VGet<S>::get(it.v)[0] = __ldg(static_cast<const T*>(kp.col[S]) + row);
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        if (ok[k]) VGet<S>::get(it[k].v)[0] = __ldg(static_cast<const T*>(kp.col[S]) + row[k]);
     }
   });
-  return true;
 }
 
 // The item loop of compacted execution (grid-stride, every lane of a warp
 // runs every trip): the first operation over whole items, its surviving rows
-// appended to the warp's queue q (kQueueCap entries in shared memory), and
-// each 32 queued rows handed one per lane to row_fn(row); the rows left at
-// the end follow.  All lanes of the warp call this together.
-template <class SH, class F>
+// appended to the warp's queue q (queue_cap<K>() entries in shared memory),
+// and each 32 * K queued rows handed K per lane to row_fn(rows, has) (lane l
+// takes entries l, l + 32, ...); the rows left at the end follow.  All lanes of
+// the warp call this together.
+template <class SH, int K, class F>
 __device__ __forceinline__ void for_rows_compacted(const KParams& kp, uint32_t* q, F&& row_fn) {
+  constexpr int QC = queue_cap<K>();
+  constexpr int KEEP = (QC - 32 * K + 31) / 32;  // entries a lane moves down after a drain
   const int lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
   int qlen = 0;  // warp-uniform
   auto drain = [&](int n) {
-    if (lane < n) row_fn(q[lane]);
-    __syncwarp();
-    uint32_t keep[(kQueueCap - 32 + 31) / 32];
+    uint32_t rows[K];
+    bool has[K];
 #pragma unroll
-    for (int i = 0; i < (kQueueCap - 32 + 31) / 32; ++i) {
+    for (int k = 0; k < K; ++k) {
+      has[k] = lane + 32 * k < n;
+      rows[k] = has[k] ? q[lane + 32 * k] : 0u;
+    }
+    if (has[0]) row_fn(rows, has);
+    __syncwarp();
+    uint32_t keep[KEEP];
+#pragma unroll
+    for (int i = 0; i < KEEP; ++i) {
       const int k = n + lane + 32 * i;
       keep[i] = k < qlen ? q[k] : 0u;
     }
     __syncwarp();
 #pragma unroll
-    for (int i = 0; i < (kQueueCap - 32 + 31) / 32; ++i) {
+    for (int i = 0; i < KEEP; ++i) {
       const int k = lane + 32 * i;
       if (k < qlen - n) q[k] = keep[i];
     }
@@ -443,7 +471,7 @@ __device__ __forceinline__ void for_rows_compacted(const KParams& kp, uint32_t* 
       qlen += __popc(b);
     }
     __syncwarp();
-    while (qlen >= 32) drain(32);
+    while (qlen >= 32 * K) drain(32 * K);
   }
   if (qlen > 0) drain(qlen);
 }

@@ -36,8 +36,8 @@ GRIDS = {
     "filter_aggregate": [dict(pred=p, access=a, items_per_thread=u, block=b, prefetch=f)
                          for p, a, u, b, f in itertools.product(["branch", "predicated"], ["grid", "chunked"],
                                                                 [1, 4], [256, 512], [0, 1])] +
-                        [dict(pred="compacted", access="grid", items_per_thread=1, block=b, prefetch=f)
-                         for b, f in itertools.product([256, 512], [0, 1])],
+                        [dict(pred="compacted", access="grid", items_per_thread=u, block=b, prefetch=f)
+                         for u, b, f in itertools.product([1, 2], [256, 512], [0, 1])],
     "filter_project": [dict(exec=e, pred=p, access=a, items_per_thread=u, block=256, prefetch=f)
                        for e, p, a, u, f in itertools.product(["single", "multi"], ["branch", "predicated"],
                                                               ["grid", "chunked"], [1, 4], [0, 1])],
@@ -54,10 +54,11 @@ GRIDS = {
                     [dict(agg="global", ht="perfect"), dict(agg="global", ht="linear"),
                      dict(agg="global", ht="linear", exec="multi"), dict(agg="global", ht="cuckoo", exec="multi")],
                     ["branch", "predicated"])] +
-               # rows passing the filter queued per warp
-               [dict(s, pred="compacted", items_per_thread=1, block=256, prefetch=0)
-                for s in [dict(agg="local", ht="perfect"), dict(agg="global", ht="perfect"),
-                          dict(agg="local", ht="linear"), dict(agg="global", ht="linear")]] +
+               # rows passing the filter queued per warp, taken 1 or 2 per lane
+               [dict(s, pred="compacted", items_per_thread=u, block=256, prefetch=0)
+                for s, u in itertools.product([dict(agg="local", ht="perfect"), dict(agg="global", ht="perfect"),
+                                               dict(agg="local", ht="linear"), dict(agg="global", ht="linear")],
+                                              [1, 2])] +
                # perfect array in the distributed shared memory of a cluster of 2 to 16 CTAs
                [dict(agg="cluster", ht="perfect", pred="branch", items_per_thread=1, block=512, prefetch=0,
                      warp_agg=w) for w in (0, 1)] +
@@ -70,11 +71,11 @@ GRIDS = {
                  [dict(agg="local", ht="perfect"), dict(agg="global", ht="perfect"),
                   dict(agg="local", ht="linear"), dict(agg="global", ht="linear")],
                  ["branch", "predicated"], [0, 1])] +
-            [dict(s, build=bk, pred="compacted", items_per_thread=1, block=512, prefetch=0)
-             for bk, s in itertools.product(
+            [dict(s, build=bk, pred="compacted", items_per_thread=u, block=512, prefetch=0)
+             for bk, s, u in itertools.product(
                  ["perfect", "linear", "cuckoo"],
                  [dict(agg="local", ht="perfect"), dict(agg="global", ht="perfect"),
-                  dict(agg="local", ht="linear"), dict(agg="global", ht="linear")])],
+                  dict(agg="local", ht="linear"), dict(agg="global", ht="linear")], [1, 2])],
 }
 
 

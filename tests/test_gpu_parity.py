@@ -520,10 +520,11 @@ def test_warp_preaggregation_min_max_join(ctx):
 
 
 # ---------------------------------------------------------------- compacted execution
-COMPACT_VARIANTS = [dict(agg=a, ht=h, pred="compacted", items_per_thread=1, threads_per_table=tp, warp_agg=wa,
+# items_per_thread: queued rows a lane takes through the row stage at once (1 or 2)
+COMPACT_VARIANTS = [dict(agg=a, ht=h, pred="compacted", items_per_thread=u, threads_per_table=tp, warp_agg=wa,
                          block=b, prefetch=pf)
-                    for a, h, tp, wa, b, pf in itertools.product(["local", "global"], ["linear", "cuckoo", "perfect"],
-                                                                 [0, 1], [0, 1], [64, 256, 1024], [0, 1])]
+                    for a, h, tp, wa, b, pf, u in itertools.product(["local", "global"], ["linear", "cuckoo", "perfect"],
+                                                                    [0, 1], [0, 1], [64, 256, 1024], [0, 1], [1, 2])]
 
 
 def _compacted(ctx, plan, tables, htv=None, step=1, min_ran=10):
@@ -554,7 +555,7 @@ def test_compacted_star_join(ctx, build_kind):
     s = _star_small(150_007, seed=33)
     register(ctx, s)
     for th in ({"d_a": 60, "d_b": 50, "d_c": 30, "d_d": 40}, {"d_a": 20, "d_b": 20, "d_c": 5, "d_d": 10}):
-        _compacted(ctx, workloads.star_plan(th), s, pv.ht_variant(build_kind), step=4, min_ran=8)
+        _compacted(ctx, workloads.star_plan(th), s, pv.ht_variant(build_kind), step=7, min_ran=8)
 
 
 def test_compacted_min_max_join_and_ragged_tables(ctx):
@@ -584,7 +585,7 @@ def test_compacted_is_unsupported_where_it_does_not_apply(ctx):
     register(ctx, kv)
     for plan, kw in ((workloads.keyval_plan(), dict()),                             # nothing to compact on
                      (workloads.keyval_plan(val_lt=5), dict(exec="multi")),         # key pass
-                     (workloads.keyval_plan(val_lt=5), dict(items_per_thread=2)),
+                     (workloads.keyval_plan(val_lt=5), dict(items_per_thread=4)),
                      (workloads.keyval_plan(val_lt=5), dict(access="chunked"))):
         with pytest.raises(pv.PVError) as e:
             ctx.query(plan, pv.variant(pred="compacted", **kw))
@@ -603,8 +604,10 @@ def test_compacted_ungrouped_aggregates(ctx, n):
     for plan in (workloads.filter_agg_plan(), workloads.filter_agg_plan(a_lt=100, b_lo=0, b_hi=99),
                  workloads.filter_agg_plan(a_lt=0)):
         w = want(plan, t)
-        for kw in (dict(block=64), dict(block=256, prefetch=1), dict(block=1024, grid_mult=1)):
-            got = ctx.query(plan, pv.variant(pred="compacted", items_per_thread=1, **kw))
+        for kw in (dict(block=64), dict(block=256, prefetch=1), dict(block=1024, grid_mult=1),
+                   dict(block=256, items_per_thread=2), dict(block=64, items_per_thread=2, grid_mult=1)):
+            kw = dict(dict(items_per_thread=1), **kw)
+            got = ctx.query(plan, pv.variant(pred="compacted", **kw))
             assert_same(got, w, ctxmsg=f"{plan['filters']} {kw}")
     kv = {"kv": datagen.table_keyval(n, 50, seed=n + 4)}
     register(ctx, kv)
