@@ -4,7 +4,7 @@
  * C ABI for the data-parallel hot path of Breß et al., "Generating Custom
  * Code for Efficient Query Execution on Heterogeneous Processors":
  *   register the columns of in-memory, column-major tables that already live
- *   in device memory (Section 7.5: column store, data cached on the device
+ *   in device memory (Section 7.6: column store, data cached on the device
  *   before execution, Section 9.1), build a hash table on a dimension in a
  *   build pipeline (Table 2; HASH_PUT of Table 1), run a probe/scan pipeline
  *   program (Table 1, Section 3.1) under one variant configuration
@@ -73,7 +73,7 @@ typedef int32_t pv_graph; /* captured-graph handle */
  * PV_PREFIX (string starts with a constant) is for pv_dict_range only; a
  * pv_pred never carries it. */
 typedef enum { PV_LT = 0, PV_LE = 1, PV_GT = 2, PV_GE = 3, PV_EQ = 4, PV_BETWEEN = 5, PV_PREFIX = 6 } pv_cmp;
-/* Distributive aggregate functions (Section 7.5). */
+/* Distributive aggregate functions (Section 7.6). */
 typedef enum { PV_SUM = 0, PV_COUNT = 1, PV_MIN = 2, PV_MAX = 3 } pv_func;
 /* ARITHMETIC term (Table 1): x, x + c or c - x; an aggregate's value is the
  * product of its terms (e.g. price * (100 - disc) * (100 + tax)). */

@@ -15,7 +15,7 @@
 //     pipeline then probes them in order (Table 2);
 //   * a probe miss drops the tuple (inner equi-join on a unique build key);
 //   * AGGREGATE / HASH_AGGREGATE use distributive aggregates only
-//     (SUM, COUNT, MIN, MAX; Section 7.5);
+//     (SUM, COUNT, MIN, MAX; Section 7.6);
 //   * PROJECT materialises the surviving tuples in input order.
 //
 // Readings where the paper is silent (kept identical on the CUDA side by

@@ -170,6 +170,30 @@ __global__ void k_perfect_bits(const uint64_t* slots, int64_t cap, uint32_t* bit
   }
 }
 
+// One byte per slot of a perfect array whose payload spans at most 255
+// values: 0 for an empty slot, else payload - base (base = smallest payload - 1).
+// A payload outside that span (the build columns changed since the first
+// build's statistics) is reported as a key outside its domain.
+__global__ void k_perfect_codes(const uint64_t* slots, int64_t cap, uint8_t* codes, int32_t base, int32_t* err) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < cap;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const uint64_t s = slots[i];
+    uint32_t c = 0;
+    if (s != 0) {
+      const int64_t d = static_cast<int64_t>(static_cast<int32_t>(s >> 32)) - base;
+      if (d < 1 || d > 255) set_error(err, PV_ERR_KEY_OUT_OF_RANGE);
+      else c = static_cast<uint32_t>(d);
+    }
+    codes[i] = static_cast<uint8_t>(c);
+  }
+}
+
+static void launch_codes(const BuildEnv& env, const DevHT& h) {
+  const int g = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(env.sm_count * 8, (h.cap + 255) / 256)));
+  k_perfect_codes<<<g, 256, 0, env.stream>>>(h.slots, h.cap, const_cast<uint8_t*>(h.codes), h.code_base, env.err);
+  ++*env.launches;
+}
+
 pv_status build_table(const BuildEnv& env, const BuildInput& in, const pv_ht_variant& var, int64_t kmin,
                       int64_t kmax, BuildTable& out, std::string& msg) {
   DevHT& h = out.ht;
@@ -236,7 +260,11 @@ pv_status build_table(const BuildEnv& env, const BuildInput& in, const pv_ht_var
   h.payload = in.n_payload > 0 ? 1 : 0;
   const size_t bits_bytes = with_bits ? static_cast<size_t>((h.cap + 31) / 32) * 4 : 0;
   constexpr size_t stats_bytes = 16 * PV_MAX_PAYLOAD;
-  out.mem = env.alloc(stats_off + stats_bytes + bits_bytes + 64, env.user);
+  // a perfect array with one payload column may turn out (payload statistics) to fit one byte per slot
+  const bool may_code = var.kind == PV_HT_PERFECT && in.n_payload == 1;
+  const size_t codes_off = stats_off + stats_bytes + ((bits_bytes + 15) & ~size_t(15));
+  const size_t codes_bytes = may_code ? static_cast<size_t>(h.cap) : 0;
+  out.mem = env.alloc(codes_off + codes_bytes + 64, env.user);
   if (!out.mem) {
     msg = "allocator returned NULL";
     return PV_ERR_OOM;
@@ -275,6 +303,13 @@ pv_status build_table(const BuildEnv& env, const BuildInput& in, const pv_ht_var
       out.pay_min[i] = decode_min(hs[2 * i + 1]);
     }
   }
+  if (may_code && out.pay_max[0] - out.pay_min[0] <= 254 && out.pay_min[0] > INT32_MIN) {
+    // probes read one byte per key instead of an 8-byte slot (and its presence bit)
+    h.codes = reinterpret_cast<const uint8_t*>(static_cast<char*>(out.mem) + codes_off);
+    h.code_base = static_cast<int32_t>(out.pay_max[0] >= out.pay_min[0] ? out.pay_min[0] - 1 : -1);
+    out.bp.ht = h;
+    launch_codes(env, h);
+  }
   return PV_OK;
 }
 
@@ -294,7 +329,8 @@ pv_status rebuild_table(const BuildEnv& env, const BuildTable& t) {
       ++*env.launches;
     }
   }
-  if (h.bits != nullptr) {
+  if (h.codes != nullptr) launch_codes(env, h);
+  if (h.bits != nullptr && h.codes == nullptr) {
     const int64_t words = (h.cap + 31) / 32;
     const int g3 = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(env.sm_count * 8, (words + 7) / 8)));
     k_perfect_bits<<<g3, 256, 0, env.stream>>>(h.slots, h.cap, const_cast<uint32_t*>(h.bits));

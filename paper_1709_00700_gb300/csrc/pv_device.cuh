@@ -34,6 +34,9 @@ struct DevHT {
   uint64_t* slots;
   const uint32_t* bits;  // perfect array without payload, or past 64 KB of slots: presence bit per
                          // slot (probes test it first, then read the slot of a hit for its payload)
+  const uint8_t* codes;  // perfect array whose one payload spans at most 255 values: one byte per
+                         // slot, 0 = empty, else payload - code_base (probes read it, not the slots)
+  int32_t code_base;
   int32_t kind;      // pv_ht_kind
   int32_t hash;      // pv_hash_fn
   int32_t log2cap;
@@ -318,6 +321,11 @@ __device__ __forceinline__ bool probe_key(const DevHT& h, int64_t key, int32_t& 
   if (h.kind == PV_HT_PERFECT) {
     const int64_t i = key - h.kmin;
     if (static_cast<uint64_t>(i) >= static_cast<uint64_t>(h.cap)) return false;
+    if (h.codes != nullptr) {  // one byte per key
+      const uint32_t b = __ldg(h.codes + i);
+      pay = b != 0u ? static_cast<int32_t>(b) + h.code_base : 0;
+      return b != 0u;
+    }
     if (h.bits != nullptr) {  // 1 bit per key instead of 8 bytes: small enough to stay in L1
       const bool hit = (__ldg(h.bits + (i >> 5)) >> (i & 31)) & 1u;
       pay = hit && h.payload ? static_cast<int32_t>(__ldg(reinterpret_cast<const unsigned long long*>(h.slots) + i) >> 32)
@@ -371,6 +379,16 @@ __device__ __forceinline__ uint32_t probe_item(const DevHT& h, const T (&fk)[4],
       // (a wrapped difference would need fk < INT32_MIN or kmin + cap > 2^31).
       if (h.narrow) {
         const uint32_t k0 = static_cast<uint32_t>(h.kmin), cap = static_cast<uint32_t>(h.cap);
+        if (h.codes != nullptr) {  // one byte per key: 4 independent loads, no slot reads
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const uint32_t i = static_cast<uint32_t>(static_cast<int32_t>(fk[r])) - k0;
+            const uint32_t b = i < cap ? static_cast<uint32_t>(__ldg(h.codes + i)) : 0u;
+            hit |= static_cast<uint32_t>(b != 0u) << r;
+            pay[r] = b != 0u ? static_cast<int32_t>(b) + h.code_base : 0;
+          }
+          return mask & hit;
+        }
         if (h.bits != nullptr) {
           uint32_t ic[4];
 #pragma unroll
@@ -402,6 +420,16 @@ __device__ __forceinline__ uint32_t probe_item(const DevHT& h, const T (&fk)[4],
         }
         return mask & hit;
       }
+    }
+    if (h.codes != nullptr) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const uint64_t i = static_cast<uint64_t>(static_cast<int64_t>(fk[r]) - h.kmin);
+        const uint32_t b = i < static_cast<uint64_t>(h.cap) ? static_cast<uint32_t>(__ldg(h.codes + i)) : 0u;
+        hit |= static_cast<uint32_t>(b != 0u) << r;
+        pay[r] = b != 0u ? static_cast<int32_t>(b) + h.code_base : 0;
+      }
+      return mask & hit;
     }
     if (h.bits != nullptr) {
       uint64_t ic[4];

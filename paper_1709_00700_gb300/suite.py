@@ -312,7 +312,7 @@ def _rows(qs, stats, timings):
     X, y = [], []
     for q in qs:
         for v in GRIDS[grid_key(q)]:
-            ms = timings[q["id"]][autotune.variant_key(v)]
+            ms = timings[q["id"]].get(autotune.variant_key(v), math.inf)
             if math.isfinite(ms):
                 X.append(costmodel.features(stats[q["id"]], v))
                 y.append(math.log(ms))
@@ -333,7 +333,7 @@ def _evaluate(model, qs, stats, timings, configs=None, top_k=3):
     out = []
     for q in qs:
         tm = timings[q["id"]]
-        finite = [v for v in GRIDS[grid_key(q)] if math.isfinite(tm[autotune.variant_key(v)])]
+        finite = [v for v in GRIDS[grid_key(q)] if math.isfinite(tm.get(autotune.variant_key(v), math.inf))]
         best = min(tm[autotune.variant_key(v)] for v in finite)
         pick, pred = costmodel.pick(model, stats[q["id"]], finite)
         ranked = [finite[i] for i in np.argsort(pred)[:top_k]]
@@ -420,7 +420,7 @@ def confirm(data: SuiteData, ex: dict, summary: dict, reps: int = 15, top: int =
         q = qmap[p["id"]]
         g = grid_key(q)
         tm = ex["timings"][q["id"]]
-        finite = sorted((v for v in GRIDS[g] if math.isfinite(tm[autotune.variant_key(v)])),
+        finite = sorted((v for v in GRIDS[g] if math.isfinite(tm.get(autotune.variant_key(v), math.inf))),
                         key=lambda v: tm[autotune.variant_key(v)])
         cands = {}
         for v in finite[:top] + [p["pick"], summary["alg1_configs"][g]]:
@@ -471,7 +471,7 @@ def online_experiment(ctx: "pv.Context", ex: dict, n_seed: int = 100, tail: int 
     r_static, r_online = [], []
     for q in stream:
         tm = timings[q["id"]]
-        finite = [v for v in GRIDS[grid_key(q)] if math.isfinite(tm[autotune.variant_key(v)])]
+        finite = [v for v in GRIDS[grid_key(q)] if math.isfinite(tm.get(autotune.variant_key(v), math.inf))]
         best = min(tm[autotune.variant_key(v)] for v in finite)
         v = tuner.choose(stats[q["id"]], finite)
         ms = tm[autotune.variant_key(v)]

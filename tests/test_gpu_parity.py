@@ -883,3 +883,61 @@ def test_probe_orders_of_the_star_join(ctx):
     got = ctx.query(plan, pv.variant(agg="global", ht="perfect", items_per_thread=1), pv.ht_variant("perfect"),
                     probe_order=(2, 0, 1, 3))
     assert_same(got, w, ctxmsg="generic (2, 0, 1, 3)")
+
+
+# ---------------------------------------------------------------- byte-coded perfect tables
+def test_byte_coded_perfect_tables(ctx):
+    """A perfect build table whose one payload spans at most 255 values is
+    probed through one byte per key; a wider payload keeps the 8-byte slots.
+    Both against the oracle, for grouping on the payload and projecting it;
+    a rebuild after an in-place change within the recorded payload range
+    stays exact, one outside it is reported (the statistics are out of date)."""
+    import torch
+    D, n = 5000, 200_003
+    rng = np.random.default_rng(31)
+    key = torch.from_numpy(rng.permutation(D).astype(np.int32)).cuda()
+    dim = {"key": key, "f": (key % 10).to(torch.int32), "narrow": (key % 40 + 5).to(torch.int32),
+           "wide": (key * 3 - 7000).to(torch.int32)}
+    fact = {"fk": torch.from_numpy(rng.integers(-50, D + 50, n).astype(np.int32)).cuda(),
+            "v": torch.from_numpy(rng.integers(0, 1000, n).astype(np.int64)).cuda()}
+    ctx.register_table("bdim", dim)
+    ctx.register_table("bfact", fact)
+
+    def host():
+        return {"bdim": {k: v.cpu().numpy() for k, v in dim.items()},
+                "bfact": {k: v.cpu().numpy() for k, v in fact.items()}}
+
+    for pay in ("narrow", "wide"):
+        build = {"table": "bdim", "key": "key", "filters": [["f", "lt", 7]], "payload": [pay]}
+        grouped = {"fact": "bfact", "builds": [build], "probes": [{"build": 0, "fk": "fk"}],
+                   "group_by": [["payload", 0, 0]], "aggs": [["sum", [["x", "v"]]], ["count"]]}
+        proj = {"fact": "bfact", "builds": [build], "probes": [{"build": 0, "fk": "fk"}],
+                "project": [["payload", 0, 0], "v"]}
+        for plan, kws in ((grouped, [dict(agg="global", ht="perfect", items_per_thread=1),
+                                     dict(agg="local", ht="perfect", pred="compacted", items_per_thread=2),
+                                     dict(agg="global", ht="linear", pred="predicated", items_per_thread=1)]),
+                          (proj, [dict(exec="multi"), dict(exec="single", interp=1)])):
+            w = want(plan, host())
+            for kw in kws:
+                got = ctx.query(plan, pv.variant(**kw), pv.ht_variant("perfect"))
+                assert_same(got, w, ordered=plan is grouped or kw.get("exec") == "multi", ctxmsg=f"{pay} {kw}")
+    # rebuilds of a byte-coded table
+    build = {"table": "bdim", "key": "key", "filters": [["f", "lt", 7]], "payload": ["narrow"]}
+    plan = {"fact": "bfact", "builds": [build], "probes": [{"build": 0, "fk": "fk"}],
+            "group_by": [["payload", 0, 0]], "aggs": [["sum", [["x", "v"]]], ["count"]]}
+    hts = ctx.build_all(plan, pv.ht_variant("perfect"))
+    res = ctx.run(plan, pv.variant(agg="global", ht="perfect", items_per_thread=1), hts)
+    ctx.sync()
+    dim["narrow"].copy_(((key * 7) % 40 + 5).to(torch.int32))  # same range of values
+    ctx.rebuild(hts[0])
+    ctx.rerun(res)
+    got = ctx.fetch(res)
+    order = np.argsort(got[0])
+    assert_same([c[order] for c in got], want(plan, host()), ctxmsg="rebuilt")
+    dim["narrow"].copy_((key % 300).to(torch.int32))  # outside the first build's payload range
+    ctx.rebuild(hts[0])
+    with pytest.raises(pv.PVError) as e:
+        ctx.sync()
+    assert e.value.status == -5
+    ctx.free(res)
+    ctx.free(hts[0])
