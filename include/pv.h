@@ -293,6 +293,21 @@ pv_status pv_register_result_column(pv_ctx* ctx, pv_res res, int32_t col, const 
  * buf[0..cap) when buf is non-NULL and cap > 0 (truncated to fit). */
 pv_status pv_result_kernel(pv_ctx* ctx, pv_res res, int32_t* generic, char* buf, int64_t cap);
 
+/* Enqueues, without synchronising, the copies of a result into caller memory:
+ * column col (its full capacity: every row the result can hold, of the
+ * column's type) to dst[col], which holds dst_rows[col] >= that capacity
+ * values, and the result's row count (int64) to *rows_dst.  dst and rows_dst
+ * are host memory (page-locked for the copies to be asynchronous) or device
+ * memory when dst_on_device.  The values are defined once the ctx stream has
+ * passed this point (pv_sync, or an event recorded after the call); rows
+ * beyond *rows_dst are undefined.  Kernel-detected errors are reported by the
+ * next pv_sync.  Lets a caller overlap the next step's input copies and
+ * kernels with this step's result copies. */
+pv_status pv_enqueue_fetch(pv_ctx* ctx, pv_res res, int32_t n_cols, void* const* dst, const int64_t* dst_rows,
+                           int64_t* rows_dst, int32_t dst_on_device);
+/* Rows a result can hold (the capacity pv_enqueue_fetch copies). */
+pv_status pv_result_capacity(pv_ctx* ctx, pv_res res, int64_t* rows);
+
 /* Releases a table, result or graph handle (columns: forgets the handle). */
 pv_status pv_free(pv_ctx* ctx, int32_t handle);
 

@@ -203,38 +203,62 @@ class OnlineTuner:
     (a run-time optimizer, the paper's future work).
 
     Every executed query contributes (its features, the measured log time of
-    the variant that ran) to a replay buffer; only the chosen variant's time
-    is observed.  With probability `explore` the network's second choice runs
-    instead of its first, so that the buffer does not only hold the variants
-    the network already likes.  Every `every` observations each network of the
-    ensemble continues training on the whole buffer for `steps` Adam steps
-    (its weights, moments and step count carry over; the standardisation
-    fitted on the seed data stays)."""
+    the variant that ran) to a replay buffer.  With observe_top = k > 1 the
+    runner-ups of the network's ranking (its 2nd .. k-th choices) are timed as
+    well, on a fraction shadow_frac of the queries: extra runs of the query
+    that cost time but show the network where its ranking is wrong, which the
+    chosen variant's time alone rarely does.  With probability `explore` the
+    network's second choice runs instead of its first.  Every `every` queries
+    each network of the ensemble continues training on the whole buffer for
+    `steps` Adam steps (its weights, moments and step count carry over; the
+    standardisation fitted on the seed data stays)."""
 
     def __init__(self, model: Ensemble, X: np.ndarray, y: np.ndarray, every: int = 16, steps: int = 400,
-                 lr: float = 5e-4, explore: float = 0.1, cap: int = 50_000, seed: int = 0):
+                 lr: float = 5e-4, explore: float = 0.1, cap: int = 50_000, seed: int = 0, observe_top: int = 1,
+                 shadow_frac: float = 1.0):
         self.model = model
         self.X = [np.asarray(x, np.float64) for x in X]
         self.y = [float(v) for v in y]
         self.every, self.steps, self.lr, self.explore, self.cap = every, steps, lr, explore, cap
+        self.observe_top, self.shadow_frac = observe_top, shadow_frac
         self.rng = np.random.default_rng(seed)
         self.pending = 0
         self.updates = 0
+        self.shadow_runs = 0
+        self._ranked = []
 
     def choose(self, stats: dict, grid: list) -> dict:
         X = np.stack([features(stats, v) for v in grid])
         order = np.argsort(self.model.predict(X))
+        self._ranked = [grid[int(i)] for i in order]
         if len(order) > 1 and self.rng.random() < self.explore:
-            return grid[int(order[1])]
-        return grid[int(order[0])]
+            return self._ranked[1]
+        return self._ranked[0]
 
-    def observe(self, stats: dict, variant: dict, ms: float):
+    def shadow_candidates(self, picked: dict) -> list:
+        """The variants to time besides the one that ran, for the last choose():
+        the top observe_top of the ranking other than `picked` (none on the
+        queries outside the shadow fraction)."""
+        if self.observe_top <= 1 or self.rng.random() >= self.shadow_frac:
+            return []
+        out = [v for v in self._ranked[:self.observe_top] if v is not picked][:self.observe_top - 1]
+        self.shadow_runs += len(out)
+        return out
+
+    def _add(self, stats: dict, variant: dict, ms: float):
         if not (ms > 0 and math.isfinite(ms)):
             return
         self.X.append(features(stats, variant))
         self.y.append(math.log(ms))
         if len(self.X) > self.cap:
             del self.X[0], self.y[0]
+
+    def observe(self, stats: dict, variant: dict, ms: float, shadows=()):
+        """One executed query: the time of the variant that ran, and the times
+        of its shadow runs [(variant, ms), ...]."""
+        self._add(stats, variant, ms)
+        for v, t in shadows:
+            self._add(stats, v, t)
         self.pending += 1
         if self.pending >= self.every:
             X, y = np.stack(self.X), np.asarray(self.y)

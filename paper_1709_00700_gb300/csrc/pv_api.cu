@@ -1112,6 +1112,56 @@ pv_status pv_fetch_results(pv_ctx* c, pv_res h, int32_t n_cols, void* const* dst
   return PV_OK;
 }
 
+static int64_t result_capacity(const Result& r) {
+  if (r.canon.mode == MODE_AGGREGATE) return 1;
+  if (r.canon.mode == MODE_PROJECT) return r.proj.capacity;
+  return r.grp.out_cap;
+}
+
+pv_status pv_result_capacity(pv_ctx* c, pv_res h, int64_t* rows) {
+  if (!c || !rows) return PV_ERR_INVALID_ARG;
+  auto it = c->results.find(h);
+  if (it == c->results.end()) return fail(c, PV_ERR_INVALID_ARG, "unknown result handle");
+  *rows = result_capacity(*it->second);
+  return PV_OK;
+}
+
+pv_status pv_enqueue_fetch(pv_ctx* c, pv_res h, int32_t n_cols, void* const* dst, const int64_t* dst_rows,
+                           int64_t* rows_dst, int32_t on_device) {
+  if (!c || !dst || !dst_rows || !rows_dst) return PV_ERR_INVALID_ARG;
+  auto it = c->results.find(h);
+  if (it == c->results.end()) return fail(c, PV_ERR_INVALID_ARG, "unknown result handle");
+  Result& r = *it->second;
+  if (n_cols != r.n_cols) return fail(c, PV_ERR_INVALID_ARG, "n_cols differs from the result's columns");
+  const int64_t cap = result_capacity(r);
+  for (int32_t col = 0; col < n_cols; ++col)
+    if (!dst[col] || dst_rows[col] < cap) return fail(c, PV_ERR_INVALID_ARG, "destination smaller than the capacity");
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  for (int32_t col = 0; col < n_cols; ++col) {
+    const void* src;
+    size_t bytes;
+    if (r.canon.mode == MODE_AGGREGATE) {
+      src = r.agg.result + col;
+      bytes = 8;
+    } else if (r.canon.mode == MODE_PROJECT) {
+      src = r.proj.col[col];
+      bytes = static_cast<size_t>(cap) * type_size(r.col_type[col]);
+    } else {
+      src = r.grp.out + static_cast<size_t>(col) * r.grp.out_cap;
+      bytes = static_cast<size_t>(cap) * 8;
+    }
+    PV_CUDA(c, cudaMemcpyAsync(dst[col], src, bytes, kind, c->stream));
+  }
+  if (r.canon.mode == MODE_AGGREGATE) {
+    *rows_dst = 1;
+  } else {
+    const void* cnt = r.canon.mode == MODE_PROJECT ? static_cast<const void*>(r.proj.count)
+                                                   : static_cast<const void*>(r.grp.out_count);
+    PV_CUDA(c, cudaMemcpyAsync(rows_dst, cnt, 8, kind, c->stream));
+  }
+  return PV_OK;
+}
+
 pv_status pv_result_kernel(pv_ctx* c, pv_res h, int32_t* generic, char* buf, int64_t cap) {
   if (!c || !generic) return PV_ERR_INVALID_ARG;
   auto it = c->results.find(h);

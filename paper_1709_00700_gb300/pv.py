@@ -110,6 +110,9 @@ _SIGS = {
     "pv_free": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
     "pv_result_kernel": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, _P(ctypes.c_int32), ctypes.c_char_p,
                                           ctypes.c_int64]),
+    "pv_result_capacity": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, _P(ctypes.c_int64)]),
+    "pv_enqueue_fetch": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_void_p),
+                                          _P(ctypes.c_int64), ctypes.c_void_p, ctypes.c_int32]),
     "pv_register_result_column": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_char_p,
                                                    ctypes.c_char_p, _P(ctypes.c_int32)]),
     "pv_graph_capture_begin": (ctypes.c_int32, [ctypes.c_void_p]),
@@ -577,6 +580,35 @@ class Context:
 
     def free(self, handle: int):
         self._check(self.lib.pv_free(self.h, handle))
+
+    def fetch_buffers(self, res: int) -> tuple:
+        """Page-locked host arrays, one per result column at the result's
+        capacity, and a page-locked row count: destinations for enqueue_fetch."""
+        import torch
+        cap = ctypes.c_int64()
+        self._check(self.lib.pv_result_capacity(self.h, res, ctypes.byref(cap)))
+        cols = []
+        m = self._n_cols(res)
+        tmap = {PV_I32: torch.int32, PV_I64: torch.int64, PV_U8: torch.uint8}
+        for c in range(m):
+            t = ctypes.c_int32()
+            self._check(self.lib.pv_result_col_type(self.h, res, c, ctypes.byref(t)))
+            cols.append(torch.empty(max(cap.value, 1), dtype=tmap[t.value]).pin_memory())
+        return cols, torch.zeros(1, dtype=torch.int64).pin_memory()
+
+    def _n_cols(self, res: int) -> int:
+        n, m = ctypes.c_int64(), ctypes.c_int32()
+        # the column count needs no synchronisation: it is a property of the plan
+        self._check(self.lib.pv_result_shape(self.h, res, ctypes.byref(n), ctypes.byref(m)))
+        return m.value
+
+    def enqueue_fetch(self, res: int, bufs: tuple):
+        """pv_enqueue_fetch into fetch_buffers(res): no synchronisation; the
+        values are there once the ctx stream has passed this point."""
+        cols, count = bufs
+        ptrs = (ctypes.c_void_p * len(cols))(*[t.data_ptr() for t in cols])
+        rows = (ctypes.c_int64 * len(cols))(*[t.numel() for t in cols])
+        self._check(self.lib.pv_enqueue_fetch(self.h, res, len(cols), ptrs, rows, ctypes.c_void_p(count.data_ptr()), 0))
 
     def result_kernel(self, res: int) -> tuple:
         """(runs on the generic kernels, canonical shape signature) of a result."""

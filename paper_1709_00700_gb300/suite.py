@@ -451,11 +451,12 @@ def confirm(data: SuiteData, ex: dict, summary: dict, reps: int = 15, top: int =
 
 def online_experiment(ctx: "pv.Context", ex: dict, n_seed: int = 100, tail: int = 100, seed_epochs: int = 10000,
                       ensemble: int = 3, lr: float = 2e-3, every: int = 16, steps: int = 400,
-                      explore: float = 0.1) -> dict:
+                      explore: float = 0.1, observe_top: int = 1, shadow_frac: float = 1.0) -> dict:
     """Run-time re-tuning: a network trained on the first n_seed queries (all
     their variants timed) then meets the other queries one at a time, in a
-    seeded random order.  For each it picks a variant, observes only that
-    variant's time (from the exhaustive timings) and learns from it
+    seeded random order.  For each it picks a variant, observes that
+    variant's time (from the exhaustive timings) and, with observe_top > 1,
+    the times of its runner-ups (shadow runs), and learns from them
     (costmodel.OnlineTuner).  Over the last `tail` queries of the stream, the
     online picks are judged against the exhaustive best beside the picks of
     the seed network left as it was."""
@@ -466,7 +467,8 @@ def online_experiment(ctx: "pv.Context", ex: dict, n_seed: int = 100, tail: int 
     X, y = _rows(seed_qs, stats, timings)
     static, _ = _fit(ctx, X, y, seed_epochs, ensemble, lr, 1709)
     online, _ = _fit(ctx, X, y, seed_epochs, ensemble, lr, 1709)
-    tuner = costmodel.OnlineTuner(online, X, y, every=every, steps=steps, explore=explore)
+    tuner = costmodel.OnlineTuner(online, X, y, every=every, steps=steps, explore=explore, observe_top=observe_top,
+                                  shadow_frac=shadow_frac)
     t0 = time.time()
     r_static, r_online = [], []
     for q in stream:
@@ -475,16 +477,22 @@ def online_experiment(ctx: "pv.Context", ex: dict, n_seed: int = 100, tail: int 
         best = min(tm[autotune.variant_key(v)] for v in finite)
         v = tuner.choose(stats[q["id"]], finite)
         ms = tm[autotune.variant_key(v)]
-        tuner.observe(stats[q["id"]], v, ms)
+        shadows = [(s_, tm[autotune.variant_key(s_)]) for s_ in tuner.shadow_candidates(v)]
+        tuner.observe(stats[q["id"]], v, ms, shadows)
         r_online.append(ms / best)
         p, _ = costmodel.pick(static, stats[q["id"]], finite)
         r_static.append(tm[autotune.variant_key(p)] / best)
     ro, rs = np.array(r_online[-tail:]), np.array(r_static[-tail:])
     gm = lambda r: float(np.exp(np.mean(np.log(r))))  # noqa: E731
+    # what the stream taught: squared error in log time on the observations the tuner collected
+    Xs, ys = np.stack(tuner.X[len(X):]), np.asarray(tuner.y[len(X):])
+    fit = {"online_fit_mse": float(np.mean((online.predict(Xs) - ys) ** 2)),
+           "static_fit_mse": float(np.mean((static.predict(Xs) - ys) ** 2)), "observations": int(len(ys))}
     return {"seed_queries": n_seed, "stream": len(stream), "tail": len(ro), "updates": tuner.updates,
-            "explore": explore, "seconds": time.time() - t0,
+            "explore": explore, "observe_top": observe_top, "shadow_frac": shadow_frac,
+            "shadow_runs_per_query": tuner.shadow_runs / max(len(stream), 1), "seconds": time.time() - t0,
             "online_within_10pct": float(np.mean(ro <= 1.10)), "online_geomean": gm(ro),
-            "static_within_10pct": float(np.mean(rs <= 1.10)), "static_geomean": gm(rs)}
+            "static_within_10pct": float(np.mean(rs <= 1.10)), "static_geomean": gm(rs), **fit}
 
 
 def run(ctx: "pv.Context", n_queries: int = 500, max_rows: int = 300_000_000, min_rows: int = 1_000_000,
@@ -538,7 +546,10 @@ def main(argv=None):
         data = data or SuiteData(ctx, a.max_rows)
         summary["confirmed"] = confirm(data, ex, summary, reps=a.confirm_reps)
     if a.online:
-        summary["online"] = online_experiment(ctx, ex)
+        # learning from the chosen variant's time alone, and from the top 3 of the ranking
+        summary["online"] = {"chosen_only": online_experiment(ctx, ex),
+                             "shadow_top3": online_experiment(ctx, ex, observe_top=3, explore=0.0, every=8,
+                                                              steps=200)}
     print(json.dumps({k: (v if k != "confirmed" else {kk: vv for kk, vv in v.items() if kk != "per_query"})
                       for k, v in summary.items() if k != "per_query"}))
     if a.out:

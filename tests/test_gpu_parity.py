@@ -914,7 +914,7 @@ def test_byte_coded_perfect_tables(ctx):
         proj = {"fact": "bfact", "builds": [build], "probes": [{"build": 0, "fk": "fk"}],
                 "project": [["payload", 0, 0], "v"]}
         for plan, kws in ((grouped, [dict(agg="global", ht="perfect", items_per_thread=1),
-                                     dict(agg="local", ht="perfect", pred="predicated", items_per_thread=1),
+                                     dict(agg="local", ht="linear", pred="predicated", items_per_thread=1),
                                      dict(agg="global", ht="linear", pred="predicated", items_per_thread=1)]),
                           (proj, [dict(exec="multi"), dict(exec="single", interp=1)])):
             w = want(plan, host())

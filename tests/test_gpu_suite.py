@@ -42,13 +42,20 @@ def test_confirm_retimes_the_held_out_candidates():
 
 
 def test_online_tuner_learns_from_its_own_runs():
+    """The run-time tuner learns from the queries it runs: after the stream,
+    its network predicts the times it observed (the chosen variants and, with
+    shadow runs, the runner-ups) better than the seed network left as it was."""
     ctx = pv.Context(0)
     data = suite.SuiteData(ctx, 2_000_000)
-    ex = suite.explore(ctx, 30, 2_000_000, 200_000, reps=2, log=None, data=data)
-    r = suite.online_experiment(ctx, ex, n_seed=10, tail=10, seed_epochs=200, ensemble=1, every=4, steps=50)
+    ex = suite.explore(ctx, 40, 2_000_000, 200_000, reps=2, log=None, data=data)
+    for top in (1, 3):
+        r = suite.online_experiment(ctx, ex, n_seed=10, tail=10, seed_epochs=300, ensemble=1, every=5, steps=200,
+                                    explore=0.0, observe_top=top)
+        assert r["stream"] == 30 and r["updates"] == 6
+        assert r["observations"] == 30 * top and r["shadow_runs_per_query"] == top - 1
+        assert r["online_fit_mse"] < r["static_fit_mse"], r
+        assert 0.0 <= r["online_within_10pct"] <= 1.0 and r["online_geomean"] >= 1.0
     ctx.close()
-    assert r["stream"] == 20 and r["updates"] == 5
-    assert 0.0 <= r["online_within_10pct"] <= 1.0 and r["online_geomean"] >= 1.0 and r["static_geomean"] >= 1.0
 
 
 def test_graph_experiment_results_equal_eager_and_oracle():
