@@ -617,7 +617,7 @@ def end_to_end(ctx, plan, var, hts, tables, dev, first, args, dist):
     pinned = {t: {c: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for c, v in cols.items()}
               for t, cols in tables.items()}
     h2d = sum(v.numel() * v.element_size() for cols in pinned.values() for v in cols.values())
-    dev2 = {t: {c: torch.empty_like(v) for c, v in cols.items()} for t, cols in dev.items()}
+    dev2 = {t: {c: v.clone() for c, v in cols.items()} for t, cols in dev.items()}  # same data: same statistics
     res = [ctx.run(plan, var, hts)]  # over dev (registered last time)
     for t, cols in dev2.items():
         ctx.register_table(t, cols)

@@ -451,7 +451,8 @@ def confirm(data: SuiteData, ex: dict, summary: dict, reps: int = 15, top: int =
 
 def online_experiment(ctx: "pv.Context", ex: dict, n_seed: int = 100, tail: int = 100, seed_epochs: int = 10000,
                       ensemble: int = 3, lr: float = 2e-3, every: int = 16, steps: int = 400,
-                      explore: float = 0.1, observe_top: int = 1, shadow_frac: float = 1.0) -> dict:
+                      explore: float = 0.1, observe_top: int = 1, shadow_frac: float = 1.0,
+                      update_lr: float = 5e-4) -> dict:
     """Run-time re-tuning: a network trained on the first n_seed queries (all
     their variants timed) then meets the other queries one at a time, in a
     seeded random order.  For each it picks a variant, observes that
@@ -467,8 +468,8 @@ def online_experiment(ctx: "pv.Context", ex: dict, n_seed: int = 100, tail: int 
     X, y = _rows(seed_qs, stats, timings)
     static, _ = _fit(ctx, X, y, seed_epochs, ensemble, lr, 1709)
     online, _ = _fit(ctx, X, y, seed_epochs, ensemble, lr, 1709)
-    tuner = costmodel.OnlineTuner(online, X, y, every=every, steps=steps, explore=explore, observe_top=observe_top,
-                                  shadow_frac=shadow_frac)
+    tuner = costmodel.OnlineTuner(online, X, y, every=every, steps=steps, lr=update_lr, explore=explore,
+                                  observe_top=observe_top, shadow_frac=shadow_frac)
     t0 = time.time()
     r_static, r_online = [], []
     for q in stream:
@@ -549,7 +550,7 @@ def main(argv=None):
         # learning from the chosen variant's time alone, and from the top 3 of the ranking
         summary["online"] = {"chosen_only": online_experiment(ctx, ex),
                              "shadow_top3": online_experiment(ctx, ex, observe_top=3, explore=0.0, every=8,
-                                                              steps=200)}
+                                                              steps=200, update_lr=1e-3)}
     print(json.dumps({k: (v if k != "confirmed" else {kk: vv for kk, vv in v.items() if kk != "per_query"})
                       for k, v in summary.items() if k != "per_query"}))
     if a.out:

@@ -279,3 +279,24 @@ def test_star_join_small_matches_bruteforce_on_sample():
     got = oracle.run(plan, small)
     assert _as_lists(got) == want["cols"]
     assert sum(want["cols"][-1]) > 0
+
+
+@pytest.mark.parametrize("n,seed,regions", [(1203, 3, 3), (2001, 4, 1), (37, 5, 5)])
+def test_chain_of_pipelines_matches_brute_force(n, seed, regions):
+    """A query of several pipelines (workloads.q5_chain, shaped like TPC-H
+    Q5): each step's result becomes a table of the next steps.  The oracle's
+    step-by-step evaluation equals the nested-loop brute force composed the
+    same way, and the per-region result adds up to the per-nation one."""
+    tables = datagen.tpch_schema(n, seed=seed)
+    chain = workloads.q5_chain(regions=regions)
+    got = oracle.run_chain(chain, tables)
+    bt = dict(tables)
+    for st, res in zip(chain, got):
+        want = bruteforce.evaluate(st["plan"], bt)
+        assert res["kind"] == want["kind"]
+        assert _as_lists(res) == want["cols"]  # projections in input order, groups by key, on both sides
+        bt[st["name"]] = {c: np.asarray(v, dtype=np.int64) for c, v in zip(st["columns"], want["cols"])}
+    nat, reg = got[2]["cols"], got[3]["cols"]
+    assert int(reg[1].sum()) == int(nat[1].sum()) and int(reg[2].sum()) == int(nat[2].sum())
+    assert int(reg[3].sum()) == len(nat[0])  # nations per region
+    assert all(int(x) // 5 < regions for x in nat[0])  # only nations of the selected regions
