@@ -523,12 +523,25 @@ def run_pv(args):
     if nv:
         nv.__enter__()
     clk.t0 = time.time()
+    step = lambda: ctx.rerun(res)  # noqa: E731
+    if args.graph:  # the step recorded once as a CUDA graph, replayed
+        import ctypes
+        ctx.rerun(res)
+        launches_graph = ctx.last_launch_count()
+        ctx._check(ctx.lib.pv_graph_capture_begin(ctx.h))
+        ctx.rerun(res)
+        g = ctypes.c_int32()
+        ctx._check(ctx.lib.pv_graph_capture_end(ctx.h, ctypes.byref(g)))
+        step = lambda: ctx._check(ctx.lib.pv_graph_launch(ctx.h, g.value))  # noqa: E731
+        for _ in range(2):
+            step()
+        ctx.sync()
     for i in range(args.steps):
         flush()  # cold L2 before every step (outside the timed events), unless --hot-l2
         starts[i].record(stream)
-        ctx.rerun(res)
+        step()
         ends[i].record(stream)
-        launches_per_step = ctx.last_launch_count()
+        launches_per_step = launches_graph if args.graph else ctx.last_launch_count()
     torch.cuda.synchronize()
     clk.t1 = time.time()
     if nv:
@@ -566,6 +579,7 @@ def run_pv(args):
                    "tuning": tuning,
                    "l2": ("hot: no flush between steps, the inputs stay in L2 (hot-L2 numbers)" if args.hot_l2 else
                           "flushed (2x L2 write, then discard) before every step, outside the timed events"),
+                   "step": "one CUDA graph replay of the pipeline" if args.graph else "one pv_rerun of the pipeline",
                    "seed": datagen.DEFAULT_SEED, "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": ncu_traffic(args.workload),
@@ -870,6 +884,8 @@ def main():
     ap.add_argument("--build-ht", default="perfect")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--graph", action="store_true",
+                    help="time replays of the step recorded as one CUDA graph instead of pv_rerun calls")
     ap.add_argument("--hot-l2", action="store_true",
                     help="no L2 flush between steps (hot-L2 numbers, labelled as such)")
     ap.add_argument("--cpu-threads", type=int, default=0, help="oracle threads (0 = all host cores)")
