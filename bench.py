@@ -70,14 +70,14 @@ Q5_NAT_GRID = [dict(agg=a, ht="perfect", pred=p, items_per_thread=u, block=b)
 # Variant per workload (measured best so far; the autotuner refreshes these).
 TUNED = {
     "lowcard": dict(agg="local", ht="perfect", threads_per_table=1, pred="predicated", access="grid",
-                    items_per_thread=1, block=256, prefetch=1),
+                    items_per_thread=1, block=256, prefetch=0),
     "filter_agg": dict(pred="branch", access="grid", items_per_thread=4, block=512, grid_mult=2),
     "filter_project": dict(exec="single", pred="branch", access="grid", items_per_thread=4, block=128),
     "keyval": dict(agg="local", ht="perfect", pred="branch", access="grid", items_per_thread=1, block=512),
-    "star": dict(agg="global", ht="perfect", pred="compacted", access="grid", items_per_thread=1, block=512),
+    "star": dict(agg="local", ht="perfect", pred="compacted", access="grid", items_per_thread=2, block=512),
     "keys3": dict(agg="local", ht="perfect", pred="branch", access="grid", items_per_thread=1, block=1024,
                   prefetch=1),
-    "star3": dict(agg="global", ht="perfect", pred="compacted", access="grid", items_per_thread=1, block=512),
+    "star3": dict(agg="local", ht="perfect", pred="compacted", access="grid", items_per_thread=2, block=512),
 }
 
 
