@@ -948,7 +948,12 @@ static pv_status run_group_compact(const LaunchCfg& c, const KParams& kp, const 
     return PV_ERR_UNSUPPORTED;  // nothing to compact on
   } else {
     // items_per_thread: queued rows a lane takes through the row stage at once
-    if (c.chunk || (c.U != 1 && c.U != 2) || kp.n_rows > static_cast<int64_t>(UINT32_MAX)) return PV_ERR_UNSUPPORTED;
+    if (c.chunk || (c.U != 1 && c.U != 2 && c.U != 4) || kp.n_rows > static_cast<int64_t>(UINT32_MAX))
+      return PV_ERR_UNSUPPORTED;
+    if (c.U == 4) {
+      const size_t smem = static_cast<size_t>(c.block / 32) * queue_cap<4>() * 4 + sink_smem;
+      return launch_k(c, k_group_compact<SH, SinkT<SH>, 4>, kp, gd, g, smem, 1);
+    }
     if (c.U == 2) {
       const size_t smem = static_cast<size_t>(c.block / 32) * queue_cap<2>() * 4 + sink_smem;
       return launch_k(c, k_group_compact<SH, SinkT<SH>, 2>, kp, gd, g, smem, 1);

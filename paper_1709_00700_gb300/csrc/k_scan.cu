@@ -366,6 +366,78 @@ __global__ void __maxnreg__(128) k_aggregate_compact(const __grid_constant__ KPa
   aggregate_epilogue<SH>(acc, out);
 }
 
+// Compacted single-pass PROJECT: the rows that survive the first operation
+// are queued per warp; at each drain every lane takes its queued rows through
+// the rest of the pipeline, the warp reserves output positions for the rows
+// that survive with one atomicAdd (ballot + popc), and each lane writes its
+// rows.  Output order is arbitrary, as for the other single-pass projection.
+template <class SH, int K>
+__global__ void __maxnreg__(128) k_project_compact(const __grid_constant__ KParams kp,
+                                                   const __grid_constant__ ProjOut out) {
+  extern __shared__ uint32_t qmem[];
+  const int lane = threadIdx.x & 31;
+  bool overflow = false;
+  for_rows_compacted<SH, K, true>(kp, qmem + (threadIdx.x >> 5) * queue_cap<K>(),
+                                  [&](const uint32_t (&rows)[K], const bool (&has)[K]) {
+    Item<SH> it[K];
+    bool ok[K];
+    compact_load_rows<SH, K>(it, ok, kp, rows, has);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const unsigned b = __ballot_sync(0xffffffffu, ok[k]);
+      if (b == 0) continue;
+      unsigned long long base = 0;
+      if (lane == 0) base = atomicAdd(out.cursor, static_cast<unsigned long long>(__popc(b)));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (ok[k]) {
+        const int64_t pos = static_cast<int64_t>(base) + __popc(b & ((1u << lane) - 1u));
+        if (pos < out.capacity) write_row<SH>(out, it[k], 0, pos);
+        else overflow = true;
+      }
+    }
+  });
+  if (overflow) set_error(kp.err, PV_ERR_OUTPUT_OVERFLOW);
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(out.done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    const int64_t n = static_cast<int64_t>(atomicExch(out.cursor, 0ull));
+    *out.count = n < out.capacity ? n : out.capacity;
+    *out.done = 0;
+  }
+}
+
+template <class SH, int K>
+static pv_status launch_proj_compact_k(const LaunchCfg& c, const KParams& kp, const ProjOut& out) {
+  auto k = k_project_compact<SH, K>;
+  const size_t smem = static_cast<size_t>(c.block / 32) * queue_cap<K>() * 4;
+  const int grid = grid_for(c, reinterpret_cast<const void*>(k), smem, kp.n_items, c.block);
+  if (grid <= 0) return PV_ERR_UNSUPPORTED;
+  kmark(c);
+  k<<<grid, c.block, smem, c.stream>>>(kp, out);
+  kmark(c);
+  ++*c.launches;
+  return cudaGetLastError() == cudaSuccess ? PV_OK : PV_ERR_CUDA;
+}
+
+template <class SH>
+static pv_status launch_proj_compact(const LaunchCfg& c, const KParams& kp, const ProjOut& out, int exec) {
+  if constexpr (SH::Where::N == 0 && SH::Probes::N == 0) {
+    return PV_ERR_UNSUPPORTED;  // nothing to compact on
+  } else {
+    // single pass only: the queues reorder rows, and multi-pass output keeps input order
+    if (exec != PV_EXEC_SINGLE_PASS || c.chunk || (c.U != 1 && c.U != 2) ||
+        kp.n_rows > static_cast<int64_t>(UINT32_MAX))
+      return PV_ERR_UNSUPPORTED;
+    return c.U == 2 ? launch_proj_compact_k<SH, 2>(c, kp, out) : launch_proj_compact_k<SH, 1>(c, kp, out);
+  }
+}
+
 template <class SH, int K>
 static pv_status launch_agg_compact_k(const LaunchCfg& c, const KParams& kp, const AggOut& out) {
   auto k = k_aggregate_compact<SH, K>;
@@ -465,8 +537,9 @@ static pv_status launch_proj(const LaunchCfg& c, const KParams& kp, const ProjOu
        {launch_proj_t<SH, false, true, 1>, launch_proj_t<SH, false, true, 2>, launch_proj_t<SH, false, true, 4>}},
       {{launch_proj_t<SH, true, false, 1>, launch_proj_t<SH, true, false, 2>, launch_proj_t<SH, true, false, 4>},
        {launch_proj_t<SH, true, true, 1>, launch_proj_t<SH, true, true, 2>, launch_proj_t<SH, true, true, 4>}}};
+  if (c.compact) return launch_proj_compact<SH>(c, kp, out, exec);
   const int ui = c.U == 1 ? 0 : c.U == 2 ? 1 : c.U == 4 ? 2 : -1;
-  if (ui < 0 || c.compact) return PV_ERR_UNSUPPORTED;  // compacted mode: aggregations only
+  if (ui < 0) return PV_ERR_UNSUPPORTED;
   return tab[c.pred][c.chunk][ui](c, kp, out, exec);
 }
 

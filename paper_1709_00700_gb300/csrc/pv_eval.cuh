@@ -333,6 +333,8 @@ template <int J, class T> struct RefPay : std::false_type {};
 template <int J, int I> struct RefPay<J, PL<J, I>> : std::true_type {};
 template <int J, template <class...> class Tm, class... Ts>
 struct RefPay<J, Tm<Ts...>> : std::bool_constant<(RefPay<J, Ts>::value || ...)> {};
+// projected values: slot S < 0 is the payload of probe -S - 1
+template <int J, int... S> struct RefPay<J, Proj<S...>> : std::bool_constant<((S == -J - 1) || ...)> {};
 
 // The row stage repeats the first probe only to bind its payload: when the
 // first operation was that probe and nothing reads its payload, it is skipped.
@@ -420,8 +422,10 @@ __device__ __forceinline__ void compact_load_rows(Item<SH> (&it)[K], bool (&ok)[
 // appended to the warp's queue q (queue_cap<K>() entries in shared memory),
 // and each 32 * K queued rows handed K per lane to row_fn(rows, has) (lane l
 // takes entries l, l + 32, ...); the rows left at the end follow.  All lanes of
-// the warp call this together.
-template <class SH, int K, class F>
+// the warp call this together.  ALL_LANES: every lane calls row_fn at every
+// drain, lanes without a row with has[] all false, so that row_fn may use warp
+// collectives; otherwise only lanes holding a row call it.
+template <class SH, int K, bool ALL_LANES = false, class F>
 __device__ __forceinline__ void for_rows_compacted(const KParams& kp, uint32_t* q, F&& row_fn) {
   constexpr int QC = queue_cap<K>();
   constexpr int KEEP = (QC - 32 * K + 31) / 32;  // entries a lane moves down after a drain
@@ -436,7 +440,7 @@ __device__ __forceinline__ void for_rows_compacted(const KParams& kp, uint32_t* 
       has[k] = lane + 32 * k < n;
       rows[k] = has[k] ? q[lane + 32 * k] : 0u;
     }
-    if (has[0]) row_fn(rows, has);
+    if (ALL_LANES || has[0]) row_fn(rows, has);
     __syncwarp();
     uint32_t keep[KEEP];
 #pragma unroll

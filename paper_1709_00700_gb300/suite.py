@@ -40,7 +40,9 @@ GRIDS = {
                          for u, b, f in itertools.product([1, 2], [256, 512], [0, 1])],
     "filter_project": [dict(exec=e, pred=p, access=a, items_per_thread=u, block=256, prefetch=f)
                        for e, p, a, u, f in itertools.product(["single", "multi"], ["branch", "predicated"],
-                                                              ["grid", "chunked"], [1, 4], [0, 1])],
+                                                              ["grid", "chunked"], [1, 4], [0, 1])] +
+                      [dict(exec="single", pred="compacted", access="grid", items_per_thread=u, block=256, prefetch=f)
+                       for u, f in itertools.product([1, 2], [0, 1])],
     "grouped": [dict(s, pred=p, items_per_thread=1, block=256, prefetch=f)
                 for s, p, f in itertools.product(
                     [dict(agg="local", ht="perfect"), dict(agg="local", ht="perfect", threads_per_table=1),
@@ -75,7 +77,7 @@ GRIDS = {
              for bk, s, u in itertools.product(
                  ["perfect", "linear", "cuckoo"],
                  [dict(agg="local", ht="perfect"), dict(agg="global", ht="perfect"),
-                  dict(agg="local", ht="linear"), dict(agg="global", ht="linear")], [1, 2])],
+                  dict(agg="local", ht="linear"), dict(agg="global", ht="linear")], [1, 2, 4])],
 }
 
 

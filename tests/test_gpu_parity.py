@@ -520,11 +520,11 @@ def test_warp_preaggregation_min_max_join(ctx):
 
 
 # ---------------------------------------------------------------- compacted execution
-# items_per_thread: queued rows a lane takes through the row stage at once (1 or 2)
+# items_per_thread: queued rows a lane takes through the row stage at once (1, 2 or 4)
 COMPACT_VARIANTS = [dict(agg=a, ht=h, pred="compacted", items_per_thread=u, threads_per_table=tp, warp_agg=wa,
                          block=b, prefetch=pf)
                     for a, h, tp, wa, b, pf, u in itertools.product(["local", "global"], ["linear", "cuckoo", "perfect"],
-                                                                    [0, 1], [0, 1], [64, 256, 1024], [0, 1], [1, 2])]
+                                                                    [0, 1], [0, 1], [64, 256, 1024], [0, 1], [1, 2, 4])]
 
 
 def _compacted(ctx, plan, tables, htv=None, step=1, min_ran=10):
@@ -543,7 +543,7 @@ def _compacted(ctx, plan, tables, htv=None, step=1, min_ran=10):
 def test_compacted_filter_first(ctx):
     li = {"li": datagen.table_lowcard_groups(40_003, seed=13)}
     register(ctx, li)
-    _compacted(ctx, workloads.lowcard_plan(day_hi=datagen.DAY0 + 300), li, step=3, min_ran=12)
+    _compacted(ctx, workloads.lowcard_plan(day_hi=datagen.DAY0 + 300), li, step=4, min_ran=12)
     for g, dist in ((1000, "zipf"), (50_000, "uniform"), (3, "uniform")):
         kv = {"kv": datagen.table_keyval(70_001, g, dist, seed=40 + g)}
         register(ctx, kv)
@@ -585,15 +585,14 @@ def test_compacted_is_unsupported_where_it_does_not_apply(ctx):
     register(ctx, kv)
     for plan, kw in ((workloads.keyval_plan(), dict()),                             # nothing to compact on
                      (workloads.keyval_plan(val_lt=5), dict(exec="multi")),         # key pass
-                     (workloads.keyval_plan(val_lt=5), dict(items_per_thread=4)),
                      (workloads.keyval_plan(val_lt=5), dict(access="chunked"))):
         with pytest.raises(pv.PVError) as e:
             ctx.query(plan, pv.variant(pred="compacted", **kw))
         assert e.value.status == -2
     t = {"t": datagen.table_filter_agg(1000)}
     register(ctx, t)
-    with pytest.raises(pv.PVError) as e:  # projections have no compacted form
-        ctx.query(workloads.filter_project_plan(), pv.variant(pred="compacted", items_per_thread=1))
+    with pytest.raises(pv.PVError) as e:  # compacted projections are single pass: queues reorder the rows
+        ctx.query(workloads.filter_project_plan(), pv.variant(pred="compacted", exec="multi", items_per_thread=1))
     assert e.value.status == -2
 
 
@@ -941,3 +940,41 @@ def test_byte_coded_perfect_tables(ctx):
     assert e.value.status == -5
     ctx.free(res)
     ctx.free(hts[0])
+
+
+
+@pytest.mark.parametrize("n", [0, 5, 4_099, 300_007])
+def test_compacted_projections(ctx, n):
+    """Single-pass PROJECT in compacted mode: the first operation's survivors
+    queued per warp, one or two per lane, output positions reserved per warp.
+    Filter-first and probe-first plans, projecting fact columns and probe
+    payloads, against the oracle as multisets; an output too small is
+    reported."""
+    t = {"t": datagen.table_filter_agg(n, seed=n + 41)}
+    register(ctx, t)
+    for plan in (workloads.filter_project_plan(), workloads.filter_project_plan(a_lt=100, b_lo=0, b_hi=99),
+                 {"fact": "t", "filters": [["a", "lt", 30]], "project": ["b", "price"]}):
+        w = want(plan, t)
+        for kw in (dict(items_per_thread=1, block=256), dict(items_per_thread=2, block=512, prefetch=1),
+                   dict(items_per_thread=2, block=64, grid_mult=1)):
+            got = ctx.query(plan, pv.variant(pred="compacted", exec="single", **kw))
+            assert_same(got, w, ordered=False, ctxmsg=f"{plan['filters']} {kw}")
+    if n:
+        s = _star_small(n, seed=n + 42)
+        for plan in ({"fact": "fact", "builds": [{"table": "d_b", "key": "key", "filters": [["f", "lt", 40]],
+                                                   "payload": ["g"]}],
+                      "probes": [{"build": 0, "fk": "fk_b"}], "project": [["payload", 0, 0], "revenue"]},
+                     {"fact": "fact", "filters": [["fk_a", "lt", 1000]],
+                      "builds": [{"table": "d_b", "key": "key", "filters": [["f", "lt", 40]], "payload": ["g"]}],
+                      "probes": [{"build": 0, "fk": "fk_b"}], "project": [["payload", 0, 0], "revenue"]}):
+            register(ctx, s)
+            w = want(plan, s)
+            for build in ("perfect", "linear"):
+                for u in (1, 2):
+                    got = ctx.query(plan, pv.variant(pred="compacted", exec="single", items_per_thread=u),
+                                    pv.ht_variant(build))
+                    assert_same(got, w, ordered=False, ctxmsg=f"{build} u={u} {plan}")
+        plan = dict(workloads.filter_project_plan(a_lt=100, b_lo=0, b_hi=99), capacity_hint=max(1, n // 3))
+        with pytest.raises(pv.PVError) as e:
+            ctx.query(plan, pv.variant(pred="compacted", exec="single", items_per_thread=1))
+        assert e.value.status == -7
