@@ -40,23 +40,37 @@ UNIT = "rows/s"
 # references (every row of every referenced column) plus what it writes.
 WORKLOADS = {
     "lowcard": dict(rows=6_000_000, bytes_per_row=4 + 1 + 1 + 4 * 8,
-                    desc="low-cardinality grouped aggregation, 6M rows, 4 groups, 8 aggregates"),
+                    desc="low-cardinality grouped aggregation, {rows} rows, 4 groups, 8 aggregates"),
     "filter_agg": dict(rows=1_000_000, bytes_per_row=16,
-                       desc="filter a<10 AND 20<=b<=40 -> SUM(price), COUNT(*), 1M rows"),
+                       desc="filter a<10 AND 20<=b<=40 -> SUM(price), COUNT(*), {rows} rows"),
     "filter_project": dict(rows=1_000_000, bytes_per_row=16,
-                           desc="filter a<10 AND 20<=b<=40 -> (a, price) rows, 1M rows"),
+                           desc="filter a<10 AND 20<=b<=40 -> (a, price) rows, {rows} rows"),
     "keyval": dict(rows=60_000_000, bytes_per_row=12,
-                   desc="SUM(val), COUNT(*) GROUP BY key, 60M rows, G groups"),
+                   desc="SUM(val), COUNT(*) GROUP BY key, {rows} rows, G groups"),
     "star": dict(rows=60_000_000, bytes_per_row=24,
-                 desc="four-probe star join grouped on two dimension attributes, 60M fact rows"),
+                 desc="four-probe star join grouped on two dimension attributes, {rows} fact rows"),
     "keys3": dict(rows=60_000_000, bytes_per_row=3 * 4 + 8,
-                  desc="SUM(val), COUNT(*) GROUP BY a, b, c (16 x 64 x 7 groups), 60M rows"),
+                  desc="SUM(val), COUNT(*) GROUP BY a, b, c (16 x 64 x 7 groups), {rows} rows"),
     "star3": dict(rows=60_000_000, bytes_per_row=3 * 4 + 8,
-                  desc="three-probe star join (SSB Q3.1 shape) grouped on three dimension attributes, 60M fact rows"),
+                  desc="three-probe star join (SSB Q3.1 shape) grouped on three dimension attributes, {rows} fact rows"),
     "q5": dict(rows=60_000_000, bytes_per_row=4 + 8 + 8,
                desc="TPC-H Q5-shaped query of four pipelines (builds over two projection results, an aggregation "
-                    "over an aggregation) replayed as one CUDA graph, 60M line items, 15M orders, 1.5M customers"),
+                    "over an aggregation) replayed as one CUDA graph, {rows} line items, {orders} orders, {customers} customers"),
 }
+
+def fmt_rows(n: int) -> str:
+    for div, sfx in ((1_000_000_000, "G"), (1_000_000, "M"), (1_000, "K")):
+        if n >= div:
+            return f"{n / div:g}{sfx}"
+    return str(n)
+
+
+def describe(name: str, rows: int) -> str:
+    """The workload's description at `rows` rows (orders and customers of the
+    multi-pipeline query scale with the line items)."""
+    return WORKLOADS[name]["desc"].format(rows=fmt_rows(rows), orders=fmt_rows(rows // 4),
+                                          customers=fmt_rows(rows // 40))
+
 
 # Variant of each step of the multi-pipeline query (the last step reads a
 # grouped result, so it runs on the generic kernels).
@@ -456,7 +470,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic (seeded counter-based generator)",
-        "config": {"workload": w["desc"], "rows": rows, "seed": datagen.DEFAULT_SEED},
+        "config": {"workload": describe(args.workload, rows), "rows": rows, "seed": datagen.DEFAULT_SEED},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"the whole {rows}-row table per step, row-partitioned over {cores} threads"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -573,7 +587,7 @@ def run_pv(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000 * total_s / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic (seeded counter-based generator)",
-        "config": {"workload": w["desc"], "rows": rows,
+        "config": {"workload": describe(args.workload, rows), "rows": rows,
                    **({"groups": args.groups, "keys": args.dist} if args.workload == "keyval" else {}),
                    "variant": dict(var_kw, build=build_ht, **({"probe_order": list(order)} if order else {})),
                    "tuning": tuning,
@@ -829,7 +843,7 @@ def run_pv_chain(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000 * total_s / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic (seeded counter-based generator)",
-        "config": {"workload": w["desc"], "rows": rows, "variants": variants, "build": args.build_ht, "tuning": tuning,
+        "config": {"workload": describe("q5", rows), "rows": rows, "variants": variants, "build": args.build_ht, "tuning": tuning,
                    "l2": ("hot: no flush between steps" if args.hot_l2 else
                           "flushed (2x L2 write, then discard) before every step, outside the timed events"),
                    "seed": datagen.DEFAULT_SEED, "parallelism": f"replicas x{world}"},
