@@ -632,8 +632,9 @@ def run_pv(args):
 def end_to_end(ctx, plan, var, hts, tables, dev, first, args, dist):
     """The metric end to end through the public API with host buffers: every
     step copies its input columns from page-locked host memory to the device
-    (a copy stream), runs the pipeline, and copies its result back to
-    page-locked host memory without synchronising (pv_enqueue_fetch).  Two
+    (a copy stream), runs the pipeline, and copies its result's live rows
+    back to page-locked host memory without synchronising
+    (pv_enqueue_fetch_rows).  Two
     device copies of the inputs alternate, so the input copies of step i + 1
     overlap the pipeline and the result copies of step i.  The host-to-device
     copy peak of this machine is measured alongside (one copy of the same
@@ -652,7 +653,6 @@ def end_to_end(ctx, plan, var, hts, tables, dev, first, args, dist):
     res.append(ctx.run(plan, var, hts))  # over dev2
     sets = [dev, dev2]
     bufs = [ctx.fetch_buffers(r) for r in res]
-    d2h = sum(t.numel() * t.element_size() for t in bufs[0][0]) + 8
     copy_stream = torch.cuda.Stream()
     copied = [torch.cuda.Event() for _ in range(2)]
     done = [torch.cuda.Event() for _ in range(2)]
@@ -670,7 +670,7 @@ def end_to_end(ctx, plan, var, hts, tables, dev, first, args, dist):
             copied[k].record(copy_stream)
         stream.wait_event(copied[k])
         ctx.rerun(res[k])
-        ctx.enqueue_fetch(res[k], bufs[k])
+        ctx.enqueue_fetch(res[k], bufs[k], live_rows=True)
         done[k].record(stream)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(dist, time.perf_counter() - t0)
@@ -680,15 +680,19 @@ def end_to_end(ctx, plan, var, hts, tables, dev, first, args, dist):
     n = int(count.item())
     nk = len(plan.get("group_by", []))
     got = [c[:n].numpy().astype(np.int64) for c in cols]
-    if nk:
-        order = np.lexsort(tuple(got[i] for i in reversed(range(nk))))
+    # the live rows crossed to the host: their bytes and the row count's
+    d2h = sum(n * c.element_size() for c in cols) + 8
+    if nk or "project" in plan:  # group order, and single-pass write order, are not defined
+        keys = nk or len(got)
+        order = np.lexsort(tuple(got[i] for i in reversed(range(keys))))
         got = [g[order] for g in got]
         want = first
-        order = np.lexsort(tuple(want[i] for i in reversed(range(nk))))
+        order = np.lexsort(tuple(want[i] for i in reversed(range(keys))))
         want = [w[order] for w in want]
-        assert all(np.array_equal(a, b) for a, b in zip(got, want)), "end-to-end result differs"
-    elif "project" not in plan:
-        assert all(np.array_equal(a, b) for a, b in zip(got, first)), "end-to-end result differs"
+    else:
+        want = first
+    assert len(got) == len(want) and all(np.array_equal(a, b) for a, b in zip(got, want)), \
+        "end-to-end result differs"
     # host-to-device peak: one page-locked copy of the same bytes
     big = torch.empty(h2d, dtype=torch.uint8).pin_memory()
     dbig = torch.empty(h2d, dtype=torch.uint8, device=stream.device)
@@ -710,7 +714,8 @@ def end_to_end(ctx, plan, var, hts, tables, dev, first, args, dist):
             "h2d": {"achieved_GBs": achieved, "peak_GBs": peak, "frac": achieved / peak,
                     "peak_source": "one page-locked host-to-device copy of the step's bytes, measured in this run"},
             "how": "input copies on a second stream into two alternating device buffer sets, result copies "
-                   "enqueued without synchronising (pv_enqueue_fetch), one synchronisation at the end"}
+                   "enqueued without synchronising (pv_enqueue_fetch_rows: the live rows only), one synchronisation at "
+                   "the end"}
 
 
 def run_pv_chain(args):

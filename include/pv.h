@@ -305,6 +305,19 @@ pv_status pv_result_kernel(pv_ctx* ctx, pv_res res, int32_t* generic, char* buf,
  * kernels with this step's result copies. */
 pv_status pv_enqueue_fetch(pv_ctx* ctx, pv_res res, int32_t n_cols, void* const* dst, const int64_t* dst_rows,
                            int64_t* rows_dst, int32_t dst_on_device);
+/* As pv_enqueue_fetch, but one kernel copies only the result's live rows:
+ * the first min(row count, capacity) rows of column col to dst[col] (which
+ * must still hold dst_rows[col] >= the capacity values: the count is not
+ * known on the host when the call is enqueued), and that number of rows
+ * (int64) to *rows_dst.  dst and rows_dst must be memory the device can
+ * write: device (or managed) memory, or page-locked host memory (written
+ * through its device address); pageable host memory is PV_ERR_INVALID_ARG.
+ * The bytes crossing to the host are those of the live rows, not of the
+ * capacity.  Defined once the ctx stream has passed this point; safe to
+ * capture in a graph.  Kernel-detected errors (an overflowing result: its
+ * first capacity rows are copied) are reported by the next pv_sync. */
+pv_status pv_enqueue_fetch_rows(pv_ctx* ctx, pv_res res, int32_t n_cols, void* const* dst, const int64_t* dst_rows,
+                                int64_t* rows_dst);
 /* Rows a result can hold (the capacity pv_enqueue_fetch copies). */
 pv_status pv_result_capacity(pv_ctx* ctx, pv_res res, int64_t* rows);
 

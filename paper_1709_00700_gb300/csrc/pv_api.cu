@@ -1162,6 +1162,101 @@ pv_status pv_enqueue_fetch(pv_ctx* c, pv_res h, int32_t n_cols, void* const* dst
   return PV_OK;
 }
 
+// Live-row copy of a result: column blockIdx.y, its first
+// min(*count, cap) rows (one row when count is null), into device-writable
+// memory (device memory or page-locked host memory through its device
+// address).  16-byte words when both ends are 16-byte aligned, else elements.
+struct FetchArgs {
+  const void* src[PV_MAX_KEYS + PV_MAX_AGGS];
+  void* dst[PV_MAX_KEYS + PV_MAX_AGGS];
+  int esize[PV_MAX_KEYS + PV_MAX_AGGS];
+  const unsigned long long* count;
+  int64_t cap;
+  int64_t* rows_dst;
+};
+
+__global__ void k_fetch_rows(const __grid_constant__ FetchArgs a) {
+  int64_t n = 1;
+  if (a.count != nullptr) {
+    const unsigned long long c = *a.count;
+    n = c < static_cast<unsigned long long>(a.cap) ? static_cast<int64_t>(c) : a.cap;
+  }
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *a.rows_dst = n;
+  const int col = blockIdx.y;
+  const int es = a.esize[col];
+  const char* s = static_cast<const char*>(a.src[col]);
+  char* d = static_cast<char*>(a.dst[col]);
+  const int64_t bytes = n * es;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (((reinterpret_cast<uintptr_t>(s) | reinterpret_cast<uintptr_t>(d)) & 15u) == 0) {
+    const int64_t nv = bytes >> 4;
+    for (int64_t i = t; i < nv; i += stride)
+      reinterpret_cast<uint4*>(d)[i] = __ldg(reinterpret_cast<const uint4*>(s) + i);
+    for (int64_t i = (nv << 4) + t; i < bytes; i += stride) d[i] = s[i];
+    return;
+  }
+  for (int64_t i = t; i < n; i += stride) {
+    if (es == 8) reinterpret_cast<uint64_t*>(d)[i] = reinterpret_cast<const uint64_t*>(s)[i];
+    else if (es == 4) reinterpret_cast<uint32_t*>(d)[i] = reinterpret_cast<const uint32_t*>(s)[i];
+    else d[i] = s[i];
+  }
+}
+
+// Device address of caller memory a kernel may write: device or managed
+// memory as is, page-locked host memory through its device alias; null for
+// pageable host memory.
+static void* device_writable(void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the error the query left
+    return nullptr;
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return p;
+  if (at.type == cudaMemoryTypeHost) return at.devicePointer;
+  return nullptr;
+}
+
+pv_status pv_enqueue_fetch_rows(pv_ctx* c, pv_res h, int32_t n_cols, void* const* dst, const int64_t* dst_rows,
+                                int64_t* rows_dst) {
+  if (!c || !dst || !dst_rows || !rows_dst) return PV_ERR_INVALID_ARG;
+  auto it = c->results.find(h);
+  if (it == c->results.end()) return fail(c, PV_ERR_INVALID_ARG, "unknown result handle");
+  Result& r = *it->second;
+  if (n_cols != r.n_cols) return fail(c, PV_ERR_INVALID_ARG, "n_cols differs from the result's columns");
+  const int64_t cap = result_capacity(r);
+  FetchArgs a{};
+  a.cap = cap;
+  a.rows_dst = static_cast<int64_t*>(device_writable(rows_dst));
+  if (!a.rows_dst) return fail(c, PV_ERR_INVALID_ARG, "row count destination is not device or page-locked memory");
+  int64_t max_bytes = 8;
+  for (int32_t col = 0; col < n_cols; ++col) {
+    if (!dst[col] || dst_rows[col] < cap) return fail(c, PV_ERR_INVALID_ARG, "destination smaller than the capacity");
+    a.dst[col] = device_writable(dst[col]);
+    if (!a.dst[col]) return fail(c, PV_ERR_INVALID_ARG, "destination is not device or page-locked memory");
+    if (r.canon.mode == MODE_AGGREGATE) {
+      a.src[col] = r.agg.result + col;
+      a.esize[col] = 8;
+    } else if (r.canon.mode == MODE_PROJECT) {
+      a.src[col] = r.proj.col[col];
+      a.esize[col] = static_cast<int>(type_size(r.col_type[col]));
+    } else {
+      a.src[col] = r.grp.out + static_cast<size_t>(col) * r.grp.out_cap;
+      a.esize[col] = 8;
+    }
+    max_bytes = std::max<int64_t>(max_bytes, cap * a.esize[col]);
+  }
+  a.count = r.canon.mode == MODE_AGGREGATE ? nullptr
+            : r.canon.mode == MODE_PROJECT ? reinterpret_cast<const unsigned long long*>(r.proj.count)
+                                           : r.grp.out_count;
+  // sized for the capacity: the live rows are not known on the host
+  const int64_t want = (max_bytes / 16 + 255) / 256;
+  const int gx = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(want, c->sm_count * 4)));
+  k_fetch_rows<<<dim3(gx, n_cols), 256, 0, c->stream>>>(a);
+  PV_CUDA(c, cudaGetLastError());
+  return PV_OK;
+}
+
 pv_status pv_result_kernel(pv_ctx* c, pv_res h, int32_t* generic, char* buf, int64_t cap) {
   if (!c || !generic) return PV_ERR_INVALID_ARG;
   auto it = c->results.find(h);

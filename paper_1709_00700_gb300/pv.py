@@ -113,6 +113,8 @@ _SIGS = {
     "pv_result_capacity": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, _P(ctypes.c_int64)]),
     "pv_enqueue_fetch": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_void_p),
                                           _P(ctypes.c_int64), ctypes.c_void_p, ctypes.c_int32]),
+    "pv_enqueue_fetch_rows": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_void_p),
+                                               _P(ctypes.c_int64), ctypes.c_void_p]),
     "pv_register_result_column": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_char_p,
                                                    ctypes.c_char_p, _P(ctypes.c_int32)]),
     "pv_graph_capture_begin": (ctypes.c_int32, [ctypes.c_void_p]),
@@ -602,13 +604,20 @@ class Context:
         self._check(self.lib.pv_result_shape(self.h, res, ctypes.byref(n), ctypes.byref(m)))
         return m.value
 
-    def enqueue_fetch(self, res: int, bufs: tuple):
+    def enqueue_fetch(self, res: int, bufs: tuple, live_rows: bool = False):
         """pv_enqueue_fetch into fetch_buffers(res): no synchronisation; the
-        values are there once the ctx stream has passed this point."""
+        values are there once the ctx stream has passed this point.  With
+        live_rows, pv_enqueue_fetch_rows: a kernel copies only the result's
+        live rows (the buffers must be page-locked or device memory)."""
         cols, count = bufs
         ptrs = (ctypes.c_void_p * len(cols))(*[t.data_ptr() for t in cols])
         rows = (ctypes.c_int64 * len(cols))(*[t.numel() for t in cols])
-        self._check(self.lib.pv_enqueue_fetch(self.h, res, len(cols), ptrs, rows, ctypes.c_void_p(count.data_ptr()), 0))
+        if live_rows:
+            self._check(self.lib.pv_enqueue_fetch_rows(self.h, res, len(cols), ptrs, rows,
+                                                       ctypes.c_void_p(count.data_ptr())))
+        else:
+            self._check(self.lib.pv_enqueue_fetch(self.h, res, len(cols), ptrs, rows,
+                                                  ctypes.c_void_p(count.data_ptr()), 0))
 
     def result_kernel(self, res: int) -> tuple:
         """(runs on the generic kernels, canonical shape signature) of a result."""
