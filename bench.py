@@ -77,9 +77,12 @@ def describe(name: str, rows: int) -> str:
 Q5_VARIANTS = {"cust": dict(exec="single", items_per_thread=1), "ord": dict(exec="single", items_per_thread=1),
                "nat": dict(agg="local", ht="perfect", items_per_thread=1, block=512),
                "region": dict(agg="global", ht="perfect")}
-Q5_NAT_GRID = [dict(agg=a, ht="perfect", pred=p, items_per_thread=u, block=b)
-               for a in ("local", "global") for p, u in (("branch", 1), ("predicated", 1), ("compacted", 1),
-                                                          ("compacted", 2)) for b in (256, 512)]
+Q5_NAT_GRID = ([dict(agg=a, ht="perfect", pred=p, items_per_thread=u, block=b)
+                for a in ("local", "global") for p, u in (("branch", 1), ("predicated", 1), ("compacted", 1),
+                                                           ("compacted", 2), ("compacted", 4)) for b in (256, 512)] +
+               [dict(agg="local", ht="perfect", threads_per_table=1, pred=p, items_per_thread=u, block=b)
+                for p, u in (("predicated", 1), ("compacted", 1), ("compacted", 2), ("compacted", 4))
+                for b in (128, 256)])
 
 # Variant per workload (measured best so far; the autotuner refreshes these).
 TUNED = {

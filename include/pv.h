@@ -156,14 +156,20 @@ typedef enum { PV_AGG_LOCAL = 0, PV_AGG_GLOBAL = 1, PV_AGG_CLUSTER = 2 } pv_agg_
  * first probe); its surviving rows are queued per warp and run one per lane through
  * the rest of the pipeline, so later operations see full warps. */
 typedef enum { PV_BRANCH = 0, PV_PREDICATED = 1, PV_COMPACTED = 2 } pv_pred_mode;
-typedef enum { PV_GRID_STRIDE = 0, PV_CHUNKED = 1 } pv_access;
+/* PV_STAGED (grouped predicated pipelines of compiled shapes, thread-private
+ * tables, items_per_thread 1, no prefetch; else PV_ERR_UNSUPPORTED): grid-stride
+ * chunks of 128 rows per warp; while a warp computes one chunk, the TMA engine
+ * copies its next chunk of every column it reads into the warp's shared-memory
+ * stage (bulk copies completing on an mbarrier).  A wait that gives up (a copy
+ * that never completes) reports PV_ERR_TIMEOUT at the next pv_sync. */
+typedef enum { PV_GRID_STRIDE = 0, PV_CHUNKED = 1, PV_STAGED = 2 } pv_access;
 
 typedef struct {
   int32_t exec;              /* pv_exec: projection single pass (warp-aggregated atomics) or
                                 count -> prefix sum -> scatter; aggregation: fused, or keys first */
   int32_t agg;               /* pv_agg_strategy for HASH_AGGREGATE */
   int32_t pred;              /* pv_pred_mode (all operations of the pipeline share it) */
-  int32_t access;            /* pv_access: coalesced grid-stride or per-thread chunks */
+  int32_t access;            /* pv_access: coalesced grid-stride, per-thread chunks, or TMA-staged chunks */
   int32_t ht;                /* pv_ht_kind of the aggregation table */
   int32_t hash;              /* pv_hash_fn of the aggregation table */
   int32_t block;             /* threads per CTA: 64..1024, multiple of 32 (0 = 256) */
@@ -260,7 +266,9 @@ pv_status pv_set_timeout_ms(pv_ctx* ctx, int64_t ms);
 pv_status pv_result_shape(pv_ctx* ctx, pv_res res, int64_t* n_rows, int32_t* n_cols);
 pv_status pv_result_col_type(pv_ctx* ctx, pv_res res, int32_t col, int32_t* type);
 /* Copies column col (n_rows values of its type) into dst, which holds
- * dst_rows values, on the device if dst_on_device else in host memory. */
+ * dst_rows values, on the device if dst_on_device else in host memory.
+ * Memory of the other kind (as the CUDA pointer attributes tell; managed
+ * memory is either) is PV_ERR_INVALID_ARG, before anything is copied. */
 pv_status pv_fetch_result(pv_ctx* ctx, pv_res res, int32_t col, void* dst, int64_t dst_rows,
                           int32_t dst_on_device);
 /* All n_cols result columns at once: column col goes to dst[col], which holds
@@ -298,7 +306,8 @@ pv_status pv_result_kernel(pv_ctx* ctx, pv_res res, int32_t* generic, char* buf,
  * column's type) to dst[col], which holds dst_rows[col] >= that capacity
  * values, and the result's row count (int64) to *rows_dst.  dst and rows_dst
  * are host memory (page-locked for the copies to be asynchronous) or device
- * memory when dst_on_device.  The values are defined once the ctx stream has
+ * memory when dst_on_device (memory of the other kind is PV_ERR_INVALID_ARG,
+ * as for pv_fetch_result).  The values are defined once the ctx stream has
  * passed this point (pv_sync, or an event recorded after the call); rows
  * beyond *rows_dst are undefined.  Kernel-detected errors are reported by the
  * next pv_sync.  Lets a caller overlap the next step's input copies and

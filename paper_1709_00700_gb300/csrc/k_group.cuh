@@ -497,14 +497,18 @@ constexpr SlotLayout make_slot_layout(int na, int ca) {
 // sums of the narrow aggregates: a row updates them only when each of its
 // narrow values is at most g.narrow_limit = (2^32 - 1) / (rows the thread
 // visits), so no field can overflow; any other row adds its codes straight
-// into the global table.  Fewer words per slot mean less shared-memory
-// traffic per row, the limit of this sink.
+// into the global table.  The launch takes the wide layout instead when the
+// narrow columns' statistics say some values exceed that limit
+// (g.narrow_max), so that such rows stay rare.  Fewer words per slot mean
+// less shared-memory traffic per row, the limit of this sink.
 template <class SH, bool NARROW = false>
 struct SinkThreadPerfect {
   // Tables of 256 threads x (cap x 16 B units) let three CTAs share an SM;
   // the predicated loop then runs without register double buffering.
   static constexpr int kRegs = 80;
   static constexpr bool kPipelined = false;
+  // TMA-staged access compiled (the loads that miss their register double buffer)
+  static constexpr bool kStaged = true;
   using A = typename SH::Aggs;
   static constexpr int NA = A::N;
   static constexpr int CA = count_index<A>();
@@ -801,6 +805,8 @@ template <class S, class = void> struct SinkIsCluster { static constexpr bool va
 template <class S> struct SinkIsCluster<S, std::void_t<decltype(S::kCluster)>> {
   static constexpr bool value = S::kCluster;
 };
+template <class S, class = void> struct SinkStaged { static constexpr bool value = false; };
+template <class S> struct SinkStaged<S, std::void_t<decltype(S::kStaged)>> { static constexpr bool value = S::kStaged; };
 template <class S, class = void> struct SinkPipelined { static constexpr bool value = true; };
 template <class S> struct SinkPipelined<S, std::void_t<decltype(S::kPipelined)>> {
   static constexpr bool value = S::kPipelined;
@@ -855,6 +861,28 @@ __global__ void __maxnreg__((GroupRegs<SH, Sink, PRED>::value)) k_group(const __
     });
   }
   pdl_launch_dependents();  // the extraction kernel may start launching now
+  sink.finish();
+}
+
+// TMA-staged access (predicated): the warps' stages and mbarriers come first
+// in shared memory, the sink's tables after them.
+template <class SH, class Sink>
+__global__ void __maxnreg__((GroupRegs<SH, Sink, true>::value)) k_group_staged(
+    const __grid_constant__ KParams kp, const __grid_constant__ GroupDesc gd, const __grid_constant__ GroupOut g) {
+  extern __shared__ unsigned long long smem[];
+  if (blockIdx.x == 0 && threadIdx.x == 0) *g.out_count = 0;  // extraction runs after this kernel
+  char* stages = reinterpret_cast<char*>(smem);
+  Sink sink(gd, g, kp.err, reinterpret_cast<unsigned long long*>(stages + stage_smem<SH>(blockDim.x >> 5)));
+  sink.init();
+  for_items_staged<SH>(kp, stages, [&](Item<SH>& it, auto full) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const bool live = (it.mask >> r) & 1u;
+      if constexpr (decltype(full)::value) sink.add(it, kp, r, live);
+      else if (r < it.nvalid) sink.add(it, kp, r, live);
+    }
+  });
+  pdl_launch_dependents();
   sink.finish();
 }
 
@@ -929,11 +957,12 @@ static pv_status launch_k(const LaunchCfg& c, K k, const KParams& kp, const Grou
   }
   const int grid = grid_for(c, reinterpret_cast<const void*>(k), smem, kp.n_items, static_cast<int64_t>(c.block) * U);
   if (grid <= 0) return PV_ERR_UNSUPPORTED;
-  // rows one thread visits, at most: its items (grid-stride or chunked) of 4 rows, or for compacted
-  // execution as many queued rows, plus one partial drain
+  // rows one thread visits, at most: its items (grid-stride, chunked or staged) of 4 rows, or for
+  // compacted execution as many queued rows, plus one partial drain
   const int64_t T = static_cast<int64_t>(grid) * c.block;
   GroupOut g2 = g;
   g2.narrow_limit = static_cast<uint64_t>(UINT32_MAX) / static_cast<uint64_t>(4 * ((kp.n_items + T - 1) / T) + 4);
+  if (g.narrow_check && g.narrow_max > g2.narrow_limit) return kNeedWide;
   kmark(c);
   k<<<grid, c.block, smem, c.stream>>>(kp, gd, g2);
   kmark(c);
@@ -1010,6 +1039,14 @@ static pv_status launch_k_cluster(const LaunchCfg& c, K k, const KParams& kp, co
 template <class SH, int UMASK, template <class> class SinkT>
 static pv_status run_group(const LaunchCfg& c, const KParams& kp, const GroupDesc& gd, const GroupOut& g, size_t smem) {
   using S = SinkT<SH>;
+  if (c.staged) {
+    if constexpr (SinkStaged<S>::value) {
+      if (c.compact || !c.pred || c.U != 1 || kp.prefetch != 0) return PV_ERR_UNSUPPORTED;
+      return launch_k(c, k_group_staged<SH, S>, kp, gd, g, stage_smem<SH>(c.block / 32) + smem, 1);
+    } else {
+      return PV_ERR_UNSUPPORTED;
+    }
+  }
   if constexpr (SinkIsCluster<S>::value) {
     if (c.compact || c.U != 1) return PV_ERR_UNSUPPORTED;
     if (c.pred) return c.chunk ? launch_k_cluster(c, k_group<SH, true, true, 1, S>, kp, gd, g, smem)
@@ -1060,7 +1097,7 @@ static pv_status launch_group(const LaunchCfg& c, const KParams& kp, const Group
   GroupOut g = g0;
   const bool multi = v.exec == PV_EXEC_MULTI_PASS;
   const bool local = v.agg == PV_AGG_LOCAL;
-  if (multi && c.compact) return PV_ERR_UNSUPPORTED;  // the key pass has no compacted form
+  if (multi && (c.compact || c.staged)) return PV_ERR_UNSUPPORTED;  // the key pass has neither form
   if (v.agg != PV_AGG_LOCAL && v.agg != PV_AGG_GLOBAL && v.agg != PV_AGG_CLUSTER) return PV_ERR_INVALID_ARG;
   if (v.agg == PV_AGG_CLUSTER) {  // perfect arrays in the distributed shared memory of a cluster
     if (g.ht != PV_HT_PERFECT || multi || v.threads_per_table == 1) return PV_ERR_UNSUPPORTED;
@@ -1089,7 +1126,14 @@ static pv_status launch_group(const LaunchCfg& c, const KParams& kp, const Group
       if constexpr (SinkThreadPerfectN<SH>::SW < SinkThreadPerfectW<SH>::SW) {
         const size_t smem = SinkThreadPerfectN<SH>::smem_bytes(g.cap, c.block);
         if (smem > 200 * 1024) return PV_ERR_UNSUPPORTED;
-        s = run_group<SH, UMASK, SinkThreadPerfectN>(c, kp, gd, g, smem);
+        GroupOut gn = g;
+        gn.narrow_check = 1;
+        s = run_group<SH, UMASK, SinkThreadPerfectN>(c, kp, gd, gn, smem);
+        if (s == kNeedWide) {
+          const size_t wsmem = SinkThreadPerfectW<SH>::smem_bytes(g.cap, c.block);
+          if (wsmem > 200 * 1024) return PV_ERR_UNSUPPORTED;
+          s = run_group<SH, UMASK, SinkThreadPerfectW>(c, kp, gd, g, wsmem);
+        }
       } else {
         const size_t smem = SinkThreadPerfectW<SH>::smem_bytes(g.cap, c.block);
         if (smem > 200 * 1024) return PV_ERR_UNSUPPORTED;

@@ -151,6 +151,7 @@ struct pv_ctx {
   std::vector<cudaEvent_t> kev;  // timing events, two per kernel
   int kev_used = 0;
   int64_t* d_stats = nullptr;
+  int64_t* d_one = nullptr;   // device int64 holding 1 (the row count of ungrouped results)
 };
 
 namespace {
@@ -448,13 +449,15 @@ static pv_status resolve_launch(pv_ctx* c, const pv_variant& v, LaunchCfg& L) {
   if (L.U != 1 && L.U != 2 && L.U != 4) return fail(c, PV_ERR_INVALID_ARG, "items_per_thread must be 1, 2 or 4");
   if (v.pred != PV_BRANCH && v.pred != PV_PREDICATED && v.pred != PV_COMPACTED)
     return fail(c, PV_ERR_INVALID_ARG, "bad pred mode");
-  if (v.access != PV_GRID_STRIDE && v.access != PV_CHUNKED) return fail(c, PV_ERR_INVALID_ARG, "bad access");
+  if (v.access != PV_GRID_STRIDE && v.access != PV_CHUNKED && v.access != PV_STAGED)
+    return fail(c, PV_ERR_INVALID_ARG, "bad access");
   if (v.exec != PV_EXEC_SINGLE_PASS && v.exec != PV_EXEC_MULTI_PASS) return fail(c, PV_ERR_INVALID_ARG, "bad exec");
   if (v.prefetch < 0 || v.prefetch > 16) return fail(c, PV_ERR_INVALID_ARG, "prefetch must be 0..16 trips");
   if (v.warp_agg != 0 && v.warp_agg != 1) return fail(c, PV_ERR_INVALID_ARG, "warp_agg must be 0 or 1");
   L.pred = v.pred == PV_PREDICATED;
   L.compact = v.pred == PV_COMPACTED;
   L.chunk = v.access == PV_CHUNKED;
+  L.staged = v.access == PV_STAGED;
   L.launches = &c->launches;
   if (c->ktime && !c->capturing) {
     L.mark = ktimer_mark;
@@ -705,6 +708,23 @@ static pv_status alloc_result(pv_ctx* c, Result& r) {
   }
   g.max_evictions = 32 * std::max(1, g.log2cap);
   g.warp_agg = r.var.warp_agg;
+  // largest value a narrow aggregate (SUM of one plain column) adds: decides
+  // whether thread-private tables may keep 32-bit fields
+  g.narrow_max = 0;
+  for (int a = 0; a < k.n_aggs; ++a) {
+    const GAgg& ag = k.gs.agg[a];
+    if (ag.func != PV_SUM || ag.n_terms != 1 || ag.t[0].kind != PV_TERM_X) continue;
+    int64_t lo, hi;
+    if (ag.t[0].x.kind == PV_REF_COL) {
+      pv_status st = column_stats(c, k.slot_col[ag.t[0].x.a], &lo, &hi);
+      if (st != PV_OK) return st;
+    } else {
+      lo = k.pay_min[ag.t[0].x.a][ag.t[0].x.b];
+      hi = k.pay_max[ag.t[0].x.a][ag.t[0].x.b];
+    }
+    if (hi < lo) continue;  // no rows
+    g.narrow_max = lo < 0 ? ~0ull : std::max<uint64_t>(g.narrow_max, static_cast<uint64_t>(hi));
+  }
   const int64_t slots = g.cap + 1;  // + side slot for the key equal to EMPTY
   g.replicas = g.ht == PV_HT_PERFECT && g.cap <= kReplicatedSlots ? kReplicas : 1;
   g.rep_stride = slots * g.stride;
@@ -734,6 +754,8 @@ static pv_status launch_result(pv_ctx* c, Result& r) {
   r.rows_cached = -1;
   Canon& k = r.canon;
   k.kp.prefetch = r.var.prefetch;
+  if (L.staged && (r.generic || k.mode != MODE_GROUPED))
+    return fail(c, PV_ERR_UNSUPPORTED, "TMA-staged access is compiled for grouped shapes only");
   if (r.generic) {
     if (k.mode == MODE_AGGREGATE) s = generic_aggregate(L, k.kp, k.gs, r.agg);
     else if (k.mode == MODE_PROJECT) s = generic_project(L, k.kp, k.gs, r.proj, r.var.exec);
@@ -776,7 +798,11 @@ pv_status pv_create(pv_ctx** out, int device, void* stream, void* (*alloc)(size_
   c->d_err = static_cast<int32_t*>(dalloc(c.get(), 256));
   if (!c->d_err) return PV_ERR_OOM;
   c->d_stats = reinterpret_cast<int64_t*>(reinterpret_cast<char*>(c->d_err) + 64);
+  c->d_one = reinterpret_cast<int64_t*>(reinterpret_cast<char*>(c->d_err) + 192);
+  static const int64_t one = 1;
   if (cudaMemsetAsync(c->d_err, 0, 256, c->stream) != cudaSuccess) return PV_ERR_CUDA;
+  if (cudaMemcpyAsync(c->d_one, &one, sizeof(one), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+    return PV_ERR_CUDA;
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return PV_ERR_CUDA;
   *out = c.release();
   return PV_OK;
@@ -1048,6 +1074,21 @@ pv_status pv_result_col_type(pv_ctx* c, pv_res h, int32_t col, int32_t* type) {
   return PV_OK;
 }
 
+// Whether caller memory p is of the kind a copy expects: device (or
+// managed) memory when on_device, else host memory (page-locked or not).  A
+// copy-engine copy to host memory given device memory, or the reverse, is
+// refused before it is issued.
+static bool dst_kind_ok(const void* p, bool on_device) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the error the query left: memory CUDA does not know is pageable host memory
+    return !on_device;
+  }
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return on_device ? at.type == cudaMemoryTypeDevice
+                   : at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+}
+
 pv_status pv_fetch_result(pv_ctx* c, pv_res h, int32_t col, void* dst, int64_t dst_rows, int32_t on_device) {
   if (!c) return PV_ERR_INVALID_ARG;
   auto it = c->results.find(h);
@@ -1060,6 +1101,8 @@ pv_status pv_fetch_result(pv_ctx* c, pv_res h, int32_t col, void* dst, int64_t d
   if (dst_rows < rows) return fail(c, PV_ERR_INVALID_ARG, "destination too small");
   if (rows == 0) return PV_OK;
   if (!dst) return fail(c, PV_ERR_INVALID_ARG, "null destination");
+  if (!dst_kind_ok(dst, on_device))
+    return fail(c, PV_ERR_INVALID_ARG, "destination memory is not of the kind on_device states");
   const void* src;
   size_t bytes;
   if (r.canon.mode == MODE_AGGREGATE) {
@@ -1090,6 +1133,8 @@ pv_status pv_fetch_results(pv_ctx* c, pv_res h, int32_t n_cols, void* const* dst
   for (int32_t col = 0; col < n_cols; ++col) {
     if (dst_rows[col] < rows) return fail(c, PV_ERR_INVALID_ARG, "destination too small");
     if (rows > 0 && !dst[col]) return fail(c, PV_ERR_INVALID_ARG, "null destination");
+    if (rows > 0 && !dst_kind_ok(dst[col], on_device))
+      return fail(c, PV_ERR_INVALID_ARG, "destination memory is not of the kind on_device states");
   }
   if (rows == 0) return PV_OK;
   for (int32_t col = 0; col < n_cols; ++col) {
@@ -1134,8 +1179,13 @@ pv_status pv_enqueue_fetch(pv_ctx* c, pv_res h, int32_t n_cols, void* const* dst
   Result& r = *it->second;
   if (n_cols != r.n_cols) return fail(c, PV_ERR_INVALID_ARG, "n_cols differs from the result's columns");
   const int64_t cap = result_capacity(r);
-  for (int32_t col = 0; col < n_cols; ++col)
+  for (int32_t col = 0; col < n_cols; ++col) {
     if (!dst[col] || dst_rows[col] < cap) return fail(c, PV_ERR_INVALID_ARG, "destination smaller than the capacity");
+    if (!dst_kind_ok(dst[col], on_device))
+      return fail(c, PV_ERR_INVALID_ARG, "destination memory is not of the kind dst_on_device states");
+  }
+  if (!dst_kind_ok(rows_dst, on_device))
+    return fail(c, PV_ERR_INVALID_ARG, "row count destination is not of the kind dst_on_device states");
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   for (int32_t col = 0; col < n_cols; ++col) {
     const void* src;
@@ -1153,7 +1203,9 @@ pv_status pv_enqueue_fetch(pv_ctx* c, pv_res h, int32_t n_cols, void* const* dst
     PV_CUDA(c, cudaMemcpyAsync(dst[col], src, bytes, kind, c->stream));
   }
   if (r.canon.mode == MODE_AGGREGATE) {
-    *rows_dst = 1;
+    // one row; device memory is written by a copy, never by the host
+    if (on_device) PV_CUDA(c, cudaMemcpyAsync(rows_dst, c->d_one, 8, cudaMemcpyDeviceToDevice, c->stream));
+    else *rows_dst = 1;
   } else {
     const void* cnt = r.canon.mode == MODE_PROJECT ? static_cast<const void*>(r.proj.count)
                                                    : static_cast<const void*>(r.grp.out_count);

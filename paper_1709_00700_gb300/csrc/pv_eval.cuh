@@ -309,6 +309,177 @@ __device__ __forceinline__ void for_items_pipelined(const KParams& kp, F&& consu
 }
 
 // ---------------------------------------------------------------------------
+// TMA-staged access (variant access = PV_STAGED), predicated pipelines.  A
+// warp's trip covers one chunk of 128 consecutive rows (32 items), as in
+// grid-stride access.  Lane 0 of the warp copies the next chunk of every
+// column the pipeline reads into the warp's shared-memory stage with bulk
+// copies (cp.async.bulk, the TMA engine) that complete on the warp's
+// mbarrier; meanwhile the warp filters and aggregates the current chunk from
+// registers.  The copies need no registers, so a warp always has its next
+// chunk in flight while it computes, which the register-loaded loop can only
+// do with a second register set.  Only whole chunks are staged: the last,
+// partial chunk of a table is loaded with plain loads.
+//
+// Row mapping: to read the stage without bank conflicts, lane l takes rows
+// 2l, 2l + 1, 64 + 2l and 64 + 2l + 1 of the chunk (every column the same
+// way); a grouped aggregation does not depend on which lane holds which row.
+// ---------------------------------------------------------------------------
+template <class SH>
+constexpr uint32_t staged_slots() { return SH::Where::slots | SH::Probes::slots | SH::rest_slots; }
+
+// Bytes of the stage columns before slot S (and of the whole stage, S = N).
+template <class SH, int S>
+constexpr int stage_offset() {
+  if constexpr (S == 0) {
+    return 0;
+  } else {
+    using T = typename At<S - 1, typename SH::Cols::L>::type::T;
+    return stage_offset<SH, S - 1>() + (((staged_slots<SH>() >> (S - 1)) & 1u) ? 128 * static_cast<int>(sizeof(T)) : 0);
+  }
+}
+template <class SH>
+constexpr int stage_bytes() { return stage_offset<SH, SH::Cols::N>(); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Waits for phase `parity` of the mbarrier to complete, for at most about
+// `limit_ns` nanoseconds; false when it gave up.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+  uint64_t t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (uint32_t i = 0;; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((i & 63u) == 63u) {
+      uint64_t t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      if (t - t0 > limit_ns) return false;
+    }
+  }
+}
+
+// Lane 0: copies chunk `chunk` (rows 128 * chunk ...) of every staged column
+// into the stage at shared address `dst`, completing on mbarrier `bar`.  The
+// chunk must lie wholly inside the table.  Column bases are 16-byte aligned
+// and a chunk of any column type is a multiple of 128 bytes, as the bulk
+// copy requires.
+template <class SH>
+__device__ __forceinline__ void stage_issue(const KParams& kp, int64_t chunk, uint32_t dst, uint32_t bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(stage_bytes<SH>())
+               : "memory");
+  static_for<SH::Cols::N>([&](auto c) {
+    constexpr int S = decltype(c)::value;
+    if constexpr ((staged_slots<SH>() >> S) & 1u) {
+      using T = typename At<S, typename SH::Cols::L>::type::T;
+      constexpr uint32_t bytes = 128 * sizeof(T);
+      const char* src = static_cast<const char*>(kp.col[S]) + chunk * bytes;
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+              dst + stage_offset<SH, S>()),
+          "l"(src), "r"(bytes), "r"(bar)
+          : "memory");
+    }
+  });
+}
+
+// A lane's 4 rows of the staged chunk (row mapping above) into item `it`.
+template <class SH>
+__device__ __forceinline__ void stage_read(Item<SH>& it, const char* stage, int lane) {
+  it.nvalid = 4;
+  it.mask = 0xFu;
+  static_for<SH::Cols::N>([&](auto c) {
+    constexpr int S = decltype(c)::value;
+    if constexpr ((staged_slots<SH>() >> S) & 1u) {
+      using T = typename At<S, typename SH::Cols::L>::type::T;
+      const char* col = stage + stage_offset<SH, S>();
+      auto& d = VGet<S>::get(it.v);
+      if constexpr (sizeof(T) == 8) {
+        const longlong2 a = *reinterpret_cast<const longlong2*>(col + 16 * lane);
+        const longlong2 b = *reinterpret_cast<const longlong2*>(col + 512 + 16 * lane);
+        d[0] = a.x; d[1] = a.y; d[2] = b.x; d[3] = b.y;
+      } else if constexpr (sizeof(T) == 4) {
+        const int2 a = *reinterpret_cast<const int2*>(col + 8 * lane);
+        const int2 b = *reinterpret_cast<const int2*>(col + 256 + 8 * lane);
+        d[0] = a.x; d[1] = a.y; d[2] = b.x; d[3] = b.y;
+      } else {
+        const uchar2 a = *reinterpret_cast<const uchar2*>(col + 2 * lane);
+        const uchar2 b = *reinterpret_cast<const uchar2*>(col + 64 + 2 * lane);
+        d[0] = a.x; d[1] = a.y; d[2] = b.x; d[3] = b.y;
+      }
+    }
+  });
+}
+
+// Shared memory of the stages: one stage per warp, then one 8-byte mbarrier
+// per warp (padded to 16 bytes); whatever follows starts 16-byte aligned.
+template <class SH>
+__host__ __device__ constexpr size_t stage_smem(int nwarps) {
+  return static_cast<size_t>(nwarps) * stage_bytes<SH>() + ((static_cast<size_t>(nwarps) * 8 + 15) & ~size_t(15));
+}
+
+// Predicated item loop over TMA-staged chunks: consume(it, full) for each
+// lane's item (full: 4 rows of a staged chunk).  All lanes of a warp run
+// every trip.  A wait that gives up (after about a second: a copy that never
+// completes) sets PV_ERR_TIMEOUT and ends the loop; the warp then waits once
+// more, again bounded, for the copy in flight before the caller goes on.
+template <class SH, class F>
+__device__ __forceinline__ void for_items_staged(const KParams& kp, char* stages, F&& consume) {
+  constexpr uint64_t kLimitNs = 1000000000ull;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  char* stage = stages + static_cast<size_t>(warp) * stage_bytes<SH>();
+  const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(stage));
+  const uint32_t bar = static_cast<uint32_t>(__cvta_generic_to_shared(stages)) +
+                       static_cast<uint32_t>(nwarps * stage_bytes<SH>() + 8 * warp);
+  const int64_t TW = static_cast<int64_t>(gridDim.x) * nwarps;
+  const int64_t n_chunks = (kp.n_items + 31) >> 5;
+  const int64_t n_full = kp.n_rows >> 7;  // chunks of 128 rows inside the table
+  int64_t c = static_cast<int64_t>(blockIdx.x) * nwarps + warp;
+  if (lane == 0) {
+    mbar_init(bar);
+    if (c < n_full) stage_issue<SH>(kp, c, dst, bar);
+  }
+  __syncwarp();
+  uint32_t parity = 0;
+  bool pending = c < n_full;  // a copy is in flight
+  for (; c < n_chunks; c += TW) {
+    Item<SH> one[1];
+    if (c < n_full) {
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(bar, parity, kLimitNs));
+      if (!ok) break;
+      parity ^= 1u;
+      pending = false;
+      stage_read<SH>(one[0], stage, lane);
+      __syncwarp();
+      if (lane == 0) {
+        // the warp's reads of the stage precede the next copy into it
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (c + TW < n_full) stage_issue<SH>(kp, c + TW, dst, bar);
+      }
+      pending = c + TW < n_full;
+      filter_probe_items<SH, 1>(one, kp);
+      consume(one[0], std::true_type{});
+    } else {
+      const int64_t idx[1] = {c * 32 + lane};
+      load_items_all<SH, 1>(one, kp, idx);
+      filter_probe_items<SH, 1>(one, kp);
+      consume(one[0], std::false_type{});
+    }
+  }
+  if (c < n_chunks) {  // gave up waiting
+    if (lane == 0) set_error(kp.err, PV_ERR_TIMEOUT);
+    if (pending) mbar_wait(bar, parity, kLimitNs);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Compacted execution (variant pred = PV_COMPACTED).  The pipeline's first
 // operation (its filters, or else its first probe) runs over whole items as
 // in branched mode; the rows it keeps are appended to a queue per warp in

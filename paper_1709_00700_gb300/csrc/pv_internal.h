@@ -17,6 +17,10 @@ namespace pv {
 enum Mode { MODE_AGGREGATE = 0, MODE_GROUPED = 1, MODE_PROJECT = 2 };
 
 // Launch shape resolved from a pv_variant.
+// Internal status of a grouped launch (never returned through the C ABI): the
+// 32-bit-field layout would send too many rows to the global table.
+constexpr pv_status kNeedWide = static_cast<pv_status>(-15);
+
 struct LaunchCfg {
   cudaStream_t stream;
   int sm_count;
@@ -26,6 +30,7 @@ struct LaunchCfg {
   bool pred;      // predicated
   bool compact;   // compacted: survivors of the first operation queued per warp (grouped pipelines)
   bool chunk;     // chunked access
+  bool staged;    // TMA-staged access (grouped predicated pipelines)
   int* launches;  // incremented per kernel launch
   // optional per-kernel timing: called right before and right after a launch
   void (*mark)(void* timer, cudaStream_t s);
@@ -124,8 +129,14 @@ struct GroupOut {
   int64_t rep_stride; // words between replicas: (cap + 1) * stride
   // Thread-private tables with 32-bit fields: a row whose field values are
   // all at most narrow_limit = (2^32 - 1) / (rows a thread visits) updates its
-  // thread's table; any other row updates the global table directly.
+  // thread's table; any other row updates the global table directly.  The
+  // launch sets narrow_limit.  narrow_max: the largest value of the columns the
+  // narrow aggregates sum, from column statistics (all ones when one can be
+  // negative); with narrow_check set, a launch whose narrow_limit is below it
+  // returns kNeedWide instead, and the wide layout runs.
   uint64_t narrow_limit;
+  uint64_t narrow_max;
+  int narrow_check;
   // Extraction (dense result columns, int64): out[c * out_cap + row].
   int64_t* out;
   int64_t out_cap;

@@ -33,7 +33,7 @@ HASH = {"murmur": 0, "multshift": 1}
 EXEC = {"single": 0, "multi": 1}
 AGG = {"local": 0, "global": 1, "cluster": 2}
 PRED = {"branch": 0, "predicated": 1, "compacted": 2}
-ACCESS = {"grid": 0, "chunked": 1}
+ACCESS = {"grid": 0, "chunked": 1, "staged": 2}
 _NP_OF = {PV_I32: np.int32, PV_I64: np.int64, PV_U8: np.uint8}
 
 
@@ -616,8 +616,11 @@ class Context:
             self._check(self.lib.pv_enqueue_fetch_rows(self.h, res, len(cols), ptrs, rows,
                                                        ctypes.c_void_p(count.data_ptr())))
         else:
+            on_device = 1 if count.is_cuda else 0
+            if any(t.is_cuda != count.is_cuda for t in cols):
+                raise ValueError("fetch buffers must all be on the host or all on the device")
             self._check(self.lib.pv_enqueue_fetch(self.h, res, len(cols), ptrs, rows,
-                                                  ctypes.c_void_p(count.data_ptr()), 0))
+                                                  ctypes.c_void_p(count.data_ptr()), on_device))
 
     def result_kernel(self, res: int) -> tuple:
         """(runs on the generic kernels, canonical shape signature) of a result."""

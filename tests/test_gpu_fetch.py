@@ -118,3 +118,24 @@ def test_live_row_fetch_refuses_pageable_memory(ctx):
     assert st == -1
     ctx.sync()
     ctx.free(res)
+
+
+def test_fetch_refuses_memory_of_the_other_kind(ctx):
+    """Device memory passed as a host destination (or the reverse) is refused
+    before any copy is issued."""
+    import torch
+    t = {"t": datagen.table_filter_agg(1000, seed=35)}
+    register(ctx, t)
+    res = ctx.run(workloads.filter_project_plan(), pv.variant(exec="multi"))
+    cols, count = ctx.fetch_buffers(res)
+    for on_device, bufs in ((0, ([c.cuda() for c in cols], count.cuda())), (1, (cols, count))):
+        dst, cnt = bufs
+        ptrs = (ctypes.c_void_p * len(dst))(*[a.data_ptr() for a in dst])
+        rows = (ctypes.c_int64 * len(dst))(*[a.numel() for a in dst])
+        st = ctx.lib.pv_enqueue_fetch(ctx.h, res, len(dst), ptrs, rows, ctypes.c_void_p(cnt.data_ptr()), on_device)
+        assert st == -1, on_device
+        st = ctx.lib.pv_fetch_results(ctx.h, res, len(dst), ptrs, rows, on_device)
+        assert st == -1, on_device
+    torch.cuda.synchronize()
+    ctx.sync()
+    ctx.free(res)

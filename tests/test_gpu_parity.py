@@ -164,27 +164,115 @@ def test_lowcard_grouped_all_variants(ctx):
     _grouped_all_variants(ctx, workloads.lowcard_plan(), li, min_ran=60)
 
 
-@pytest.mark.parametrize("n,big", [(60_001, 0.001), (4_099, 0.3), (1_000_003, 0.00001)])
-def test_lowcard_thread_private_32bit_fields(ctx, n, big):
+@pytest.mark.parametrize("n,big,near", [(60_001, 0.001, False), (4_099, 0.3, False), (1_000_003, 0.00001, False),
+                                        (300_007, 0.5, True), (2_000_003, 0.01, True)])
+def test_lowcard_thread_private_32bit_fields(ctx, n, big, near):
     """Thread-private tables keep the plain-column sums and the count in 32-bit
-    fields; rows whose values could overflow a field (here: large and negative
-    quantities and prices, a fraction `big` of the rows) go straight to the
-    global table.  Both paths, exact against the oracle."""
+    fields.  Rows with a value beyond 32 bits or negative (here: quantities
+    and prices of a fraction `big` of the rows) go straight to the global
+    table; a field whose sum would carry out of 32 bits flushes its exact sum
+    into the global table (near: the picked prices lie in [2^31, 2^32), so a
+    thread's field overflows every few rows).  All paths, exact against the
+    oracle."""
     li = datagen.table_lowcard_groups(n, seed=n)
     rng = np.random.default_rng(n)
     pick = rng.random(n) < big
-    li["qty"] = np.where(pick, rng.integers(-2**40, 2**40, n), li["qty"]).astype(np.int64)
+    if not near:
+        li["qty"] = np.where(pick, rng.integers(-2**40, 2**40, n), li["qty"]).astype(np.int64)
     pick = rng.random(n) < big
-    li["price"] = np.where(pick, rng.integers(2**31, 2**33, n), li["price"]).astype(np.int64)
+    hi = 2**32 if near else 2**33
+    li["price"] = np.where(pick, rng.integers(2**31, hi, n), li["price"]).astype(np.int64)
     t = {"li": li}
     register(ctx, t)
     w = want(workloads.lowcard_plan(), t)
     for kw in (dict(pred="predicated"), dict(pred="branch"), dict(pred="compacted"),
-               dict(pred="predicated", block=1024, grid_mult=1), dict(pred="branch", prefetch=1, block=64)):
+               dict(pred="predicated", block=1024, grid_mult=1), dict(pred="branch", prefetch=1, block=64),
+               dict(pred="predicated", access="staged")):
         kw = dict(kw, agg="local", ht="perfect", threads_per_table=1, items_per_thread=1)
         got = run_or_skip(ctx, workloads.lowcard_plan(), pv.variant(**kw))
         if got is not None:
             assert_same(got, w, ctxmsg=str(kw))
+
+
+@pytest.mark.parametrize("access", ["grid", "staged"])
+def test_lowcard_32bit_fields_with_stale_statistics(ctx, access):
+    """The 32-bit-field layout is chosen from the column statistics taken when
+    the pipeline is created.  Values written in place afterwards that exceed
+    a field's per-row limit (large and negative prices) take the row to the
+    global table, still exact; a new pipeline over the changed column reads
+    fresh statistics and takes the 64-bit layout."""
+    import torch
+    n = 400_003
+    li = datagen.table_lowcard_groups(n, seed=91)
+    dev = {c: torch.from_numpy(np.ascontiguousarray(v)).cuda() for c, v in li.items()}
+    ctx.register_table("li", dev)
+    plan = workloads.lowcard_plan()
+    kw = dict(agg="local", ht="perfect", threads_per_table=1, pred="predicated", access=access, items_per_thread=1)
+    res = ctx.run(plan, pv.variant(**kw))
+    rng = np.random.default_rng(92)
+    pick = rng.random(n) < 0.01
+    li["price"] = np.where(pick, rng.integers(-2**33, 2**33, n), li["price"]).astype(np.int64)
+    dev["price"].copy_(torch.from_numpy(li["price"]))
+    torch.cuda.synchronize()
+    ctx.rerun(res)
+    w = want(plan, {"li": li})
+    got = [c.astype(np.int64) for c in ctx.fetch(res)]
+    assert_same(got, w, ordered=False, ctxmsg=f"stale statistics, {access}")
+    ctx.free(res)
+    ctx.register_table("li", dev)  # fresh handles: fresh statistics
+    assert_same(ctx.query(plan, pv.variant(**kw)), w, ctxmsg=f"fresh statistics, {access}")
+
+
+STAGED = dict(agg="local", ht="perfect", threads_per_table=1, pred="predicated", access="staged",
+              items_per_thread=1)
+
+
+@pytest.mark.parametrize("n", [0, 1, 127, 128, 129, 4096 * 3 + 5, 100_003, 1_000_064])
+def test_staged_access_lowcard(ctx, n):
+    """TMA-staged chunks of 128 rows (bulk copies into per-warp stages) and the
+    plain-loaded partial chunk at the end, with the 32-bit field overflow path
+    (a few large values), against the oracle; block sizes change the warps
+    per CTA and the chunks per warp."""
+    li = datagen.table_lowcard_groups(n, seed=n + 7)
+    rng = np.random.default_rng(n)
+    pick = rng.random(n) < 0.001
+    li["price"] = np.where(pick, rng.integers(2**31, 2**33, n), li["price"]).astype(np.int64)
+    t = {"li": li}
+    register(ctx, t)
+    w = want(workloads.lowcard_plan(), t)
+    ran = 0
+    for block, gm in ((64, 0), (256, 0), (256, 1), (512, 0)):
+        got = run_or_skip(ctx, workloads.lowcard_plan(), pv.variant(**STAGED, block=block, grid_mult=gm))
+        if got is not None:
+            ran += 1
+            assert_same(got, w, ctxmsg=f"staged block {block} grid_mult {gm}")
+    assert ran >= 3
+
+
+@pytest.mark.parametrize("g", [1, 5, 10])
+def test_staged_access_keyval(ctx, g):
+    kv = {"kv": datagen.table_keyval(300_017, g, "uniform", seed=g + 3)}
+    register(ctx, kv)
+    for plan in (workloads.keyval_plan(), workloads.keyval_plan(val_lt=300_000)):
+        got = ctx.query(plan, pv.variant(**STAGED, block=256))
+        assert_same(got, want(plan, kv), ctxmsg=f"staged G={g}")
+
+
+def test_staged_access_unsupported_forms(ctx):
+    li = {"li": datagen.table_lowcard_groups(10_000, seed=3)}
+    fa = {"t": datagen.table_filter_agg(10_000, seed=3)}
+    register(ctx, li)
+    register(ctx, fa)
+    plan = workloads.lowcard_plan()
+    for kw in (dict(pred="branch"), dict(pred="compacted"), dict(items_per_thread=2), dict(prefetch=1),
+               dict(agg="global"), dict(threads_per_table=0), dict(exec="multi")):
+        with pytest.raises(pv.PVError) as e:
+            ctx.query(plan, pv.variant(**dict(STAGED, **kw)))
+        assert e.value.status == -2, kw
+    with pytest.raises(pv.PVError) as e:  # not a grouped pipeline
+        ctx.query(workloads.filter_agg_plan(), pv.variant(pred="predicated", access="staged", items_per_thread=1))
+    assert e.value.status == -2
+    ctx.sync()
 
 
 @pytest.mark.parametrize("g,dist", [(1, "uniform"), (10, "zipf"), (1000, "uniform"), (1000, "zipf"),
