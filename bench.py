@@ -94,7 +94,8 @@ TUNED = {
     "star": dict(agg="local", ht="perfect", pred="compacted", access="grid", items_per_thread=2, block=512),
     "keys3": dict(agg="local", ht="perfect", pred="branch", access="grid", items_per_thread=1, block=1024,
                   prefetch=1),
-    "star3": dict(agg="local", ht="perfect", pred="compacted", access="grid", items_per_thread=2, block=512),
+    "star3": dict(agg="local", ht="perfect", pred="compacted", access="grid", items_per_thread=1, block=256,
+                  compact_probes=2),
 }
 
 

@@ -191,6 +191,11 @@ typedef struct {
                                 and global or CTA-local tables; the other axes (chunked access, compacted
                                 mode, thread-private and cluster tables, warp pre-aggregation) return
                                 PV_ERR_UNSUPPORTED there. */
+  int32_t compact_probes;    /* PV_COMPACTED, grouped pipelines without filters: probes the first stage
+                                runs over whole items before queueing the survivors, 1 (0 = 1) or 2.
+                                With 2, the second probe's key column is read in full instead of being
+                                gathered for the queued rows; ungrouped pipelines and pipelines with
+                                filters or one probe return PV_ERR_UNSUPPORTED for 2. */
   uint64_t seed;             /* aggregation hash seeds */
 } pv_variant;
 

@@ -887,9 +887,10 @@ __global__ void __maxnreg__((GroupRegs<SH, Sink, true>::value)) k_group_staged(
 }
 
 // Compacted execution of a grouped pipeline: for_rows_compacted queues the
-// survivors of the first operation per warp; each queued row runs the other
-// probes, the sink's column loads and the sink, one row per lane.
-template <class SH, class Sink, int K>
+// survivors of the first stage (the filters, else the first NF probes) per
+// warp; each queued row runs the other probes, the sink's column loads and
+// the sink, K rows per lane.
+template <class SH, class Sink, int K, int NF>
 __global__ void __maxnreg__((GroupRegs<SH, Sink, false>::value)) k_group_compact(
     const __grid_constant__ KParams kp, const __grid_constant__ GroupDesc gd, const __grid_constant__ GroupOut g) {
   extern __shared__ unsigned long long smem[];
@@ -898,10 +899,10 @@ __global__ void __maxnreg__((GroupRegs<SH, Sink, false>::value)) k_group_compact
   if (blockIdx.x == 0 && threadIdx.x == 0) *g.out_count = 0;  // extraction runs after this kernel
   Sink sink(gd, g, kp.err, smem + nwarps * queue_cap<K>() / 2);  // the queues, 4 bytes an entry
   sink.init();
-  for_rows_compacted<SH, K>(kp, q, [&](const uint32_t (&rows)[K], const bool (&has)[K]) {
+  for_rows_compacted<SH, K, NF>(kp, q, [&](const uint32_t (&rows)[K], const bool (&has)[K]) {
     Item<SH> it[K];
     bool ok[K];
-    compact_load_rows<SH, K>(it, ok, kp, rows, has);
+    compact_load_rows<SH, K, NF>(it, ok, kp, rows, has);
 #pragma unroll
     for (int k = 0; k < K; ++k)
       if (ok[k]) sink.add(it[k], kp, 0, true);
@@ -970,6 +971,21 @@ static pv_status launch_k(const LaunchCfg& c, K k, const KParams& kp, const Grou
   return cudaGetLastError() == cudaSuccess ? PV_OK : PV_ERR_CUDA;
 }
 
+template <class SH, template <class> class SinkT, int NF>
+static pv_status run_group_compact_nf(const LaunchCfg& c, const KParams& kp, const GroupDesc& gd, const GroupOut& g,
+                                      size_t sink_smem) {
+  if (c.U == 4) {
+    const size_t smem = static_cast<size_t>(c.block / 32) * queue_cap<4>() * 4 + sink_smem;
+    return launch_k(c, k_group_compact<SH, SinkT<SH>, 4, NF>, kp, gd, g, smem, 1);
+  }
+  if (c.U == 2) {
+    const size_t smem = static_cast<size_t>(c.block / 32) * queue_cap<2>() * 4 + sink_smem;
+    return launch_k(c, k_group_compact<SH, SinkT<SH>, 2, NF>, kp, gd, g, smem, 1);
+  }
+  const size_t smem = static_cast<size_t>(c.block / 32) * queue_cap<1>() * 4 + sink_smem;
+  return launch_k(c, k_group_compact<SH, SinkT<SH>, 1, NF>, kp, gd, g, smem, 1);
+}
+
 template <class SH, template <class> class SinkT>
 static pv_status run_group_compact(const LaunchCfg& c, const KParams& kp, const GroupDesc& gd, const GroupOut& g,
                                    size_t sink_smem) {
@@ -979,16 +995,12 @@ static pv_status run_group_compact(const LaunchCfg& c, const KParams& kp, const 
     // items_per_thread: queued rows a lane takes through the row stage at once
     if (c.chunk || (c.U != 1 && c.U != 2 && c.U != 4) || kp.n_rows > static_cast<int64_t>(UINT32_MAX))
       return PV_ERR_UNSUPPORTED;
-    if (c.U == 4) {
-      const size_t smem = static_cast<size_t>(c.block / 32) * queue_cap<4>() * 4 + sink_smem;
-      return launch_k(c, k_group_compact<SH, SinkT<SH>, 4>, kp, gd, g, smem, 1);
+    if (c.compact_probes == 2) {
+      // a second first-stage probe: only pipelines of two or more probes and no filters
+      if constexpr (SH::Where::N == 0 && SH::Probes::N >= 2) return run_group_compact_nf<SH, SinkT, 2>(c, kp, gd, g, sink_smem);
+      else return PV_ERR_UNSUPPORTED;
     }
-    if (c.U == 2) {
-      const size_t smem = static_cast<size_t>(c.block / 32) * queue_cap<2>() * 4 + sink_smem;
-      return launch_k(c, k_group_compact<SH, SinkT<SH>, 2>, kp, gd, g, smem, 1);
-    }
-    const size_t smem = static_cast<size_t>(c.block / 32) * queue_cap<1>() * 4 + sink_smem;
-    return launch_k(c, k_group_compact<SH, SinkT<SH>, 1>, kp, gd, g, smem, 1);
+    return run_group_compact_nf<SH, SinkT, 1>(c, kp, gd, g, sink_smem);
   }
 }
 

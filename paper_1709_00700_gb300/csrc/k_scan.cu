@@ -347,11 +347,11 @@ __global__ void __maxnreg__(128) k_aggregate_compact(const __grid_constant__ KPa
   uint64_t acc[NA + 1];
 #pragma unroll
   for (int a = 0; a <= NA; ++a) acc[a] = 0;
-  for_rows_compacted<SH, K>(kp, qmem + (threadIdx.x >> 5) * queue_cap<K>(),
+  for_rows_compacted<SH, K, 1>(kp, qmem + (threadIdx.x >> 5) * queue_cap<K>(),
                             [&](const uint32_t (&rows)[K], const bool (&has)[K]) {
     Item<SH> it[K];
     bool ok[K];
-    compact_load_rows<SH, K>(it, ok, kp, rows, has);
+    compact_load_rows<SH, K, 1>(it, ok, kp, rows, has);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       if (!ok[k]) continue;
@@ -366,36 +366,109 @@ __global__ void __maxnreg__(128) k_aggregate_compact(const __grid_constant__ KPa
   aggregate_epilogue<SH>(acc, out);
 }
 
+// Bytes of one projected row before projected column C (source column types;
+// payloads are int32); proj_offset<SH, N> is the whole row.
+template <class SH, int C>
+constexpr int proj_offset() {
+  if constexpr (C == 0) {
+    return 0;
+  } else {
+    constexpr int S = SH::Proj::slot_of[C - 1];
+    constexpr int sz = S >= 0 ? static_cast<int>(sizeof(typename At<(S >= 0 ? S : 0), typename SH::Cols::L>::type::T)) : 4;
+    return proj_offset<SH, C - 1>() + sz;
+  }
+}
+
+// Output rows a warp stages in shared memory before it reserves their
+// positions: a flush starts at 64 rows, and one drain adds at most 32 * K.
+template <int K>
+__host__ __device__ constexpr int out_stage_rows() { return 32 * (2 + K); }
+template <class SH, int K>
+__host__ __device__ constexpr size_t out_stage_bytes() {
+  return (static_cast<size_t>(out_stage_rows<K>()) * proj_offset<SH, SH::Proj::N>() + 15) & ~size_t(15);
+}
+
+// Row `slot` of a warp's output stage (column C at stage + rows * offset(C)).
+template <class SH, int K>
+__device__ __forceinline__ void stage_out_row(char* st, int slot, Item<SH>& it) {
+  using PJ = typename SH::Proj;
+  static_for<PJ::N>([&](auto c) {
+    constexpr int C = decltype(c)::value;
+    constexpr int S = PJ::slot_of[C];
+    char* col = st + out_stage_rows<K>() * proj_offset<SH, C>();
+    if constexpr (S >= 0) {
+      using T = typename At<S, typename SH::Cols::L>::type::T;
+      reinterpret_cast<T*>(col)[slot] = VGet<S>::get(it.v)[0];
+    } else {
+      reinterpret_cast<int32_t*>(col)[slot] = it.pay[-S - 1][0];
+    }
+  });
+}
+
+// The warp's n staged rows to the output at positions reserved with one
+// atomicAdd; rows past the capacity are dropped (overflow).  All lanes.
+template <class SH, int K>
+__device__ __forceinline__ void flush_out_rows(const char* st, int n, const ProjOut& out, bool& overflow) {
+  using PJ = typename SH::Proj;
+  const int lane = threadIdx.x & 31;
+  __syncwarp();
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(out.cursor, static_cast<unsigned long long>(n));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  for (int i = lane; i < n; i += 32) {
+    const int64_t pos = static_cast<int64_t>(base) + i;
+    if (pos >= out.capacity) {
+      overflow = true;
+      continue;
+    }
+    static_for<PJ::N>([&](auto c) {
+      constexpr int C = decltype(c)::value;
+      constexpr int S = PJ::slot_of[C];
+      const char* col = st + out_stage_rows<K>() * proj_offset<SH, C>();
+      if constexpr (S >= 0) {
+        using T = typename At<S, typename SH::Cols::L>::type::T;
+        static_cast<T*>(out.col[C])[pos] = reinterpret_cast<const T*>(col)[i];
+      } else {
+        static_cast<int32_t*>(out.col[C])[pos] = reinterpret_cast<const int32_t*>(col)[i];
+      }
+    });
+  }
+  __syncwarp();
+}
+
 // Compacted single-pass PROJECT: the rows that survive the first operation
 // are queued per warp; at each drain every lane takes its queued rows through
-// the rest of the pipeline, the warp reserves output positions for the rows
-// that survive with one atomicAdd (ballot + popc), and each lane writes its
-// rows.  Output order is arbitrary, as for the other single-pass projection.
+// the rest of the pipeline, and the rows that survive are appended to the
+// warp's output stage in shared memory (ballot + popc).  Once 64 or more are
+// staged the warp reserves their output positions with one atomicAdd and
+// writes them out coalesced: one atomic per 64 to 127 output rows, where one
+// per drain put the whole grid on one counter.  Output order is arbitrary, as
+// for the other single-pass projection.
 template <class SH, int K>
 __global__ void __maxnreg__(128) k_project_compact(const __grid_constant__ KParams kp,
                                                    const __grid_constant__ ProjOut out) {
   extern __shared__ uint32_t qmem[];
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  char* ost = reinterpret_cast<char*>(qmem + nwarps * queue_cap<K>()) + warp * out_stage_bytes<SH, K>();
   bool overflow = false;
-  for_rows_compacted<SH, K, true>(kp, qmem + (threadIdx.x >> 5) * queue_cap<K>(),
-                                  [&](const uint32_t (&rows)[K], const bool (&has)[K]) {
+  int staged = 0;  // warp-uniform
+  for_rows_compacted<SH, K, 1, true>(kp, qmem + warp * queue_cap<K>(),
+                                     [&](const uint32_t (&rows)[K], const bool (&has)[K]) {
     Item<SH> it[K];
     bool ok[K];
-    compact_load_rows<SH, K>(it, ok, kp, rows, has);
+    compact_load_rows<SH, K, 1>(it, ok, kp, rows, has);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const unsigned b = __ballot_sync(0xffffffffu, ok[k]);
-      if (b == 0) continue;
-      unsigned long long base = 0;
-      if (lane == 0) base = atomicAdd(out.cursor, static_cast<unsigned long long>(__popc(b)));
-      base = __shfl_sync(0xffffffffu, base, 0);
-      if (ok[k]) {
-        const int64_t pos = static_cast<int64_t>(base) + __popc(b & ((1u << lane) - 1u));
-        if (pos < out.capacity) write_row<SH>(out, it[k], 0, pos);
-        else overflow = true;
-      }
+      if (ok[k]) stage_out_row<SH, K>(ost, staged + __popc(b & ((1u << lane) - 1u)), it[k]);
+      staged += __popc(b);
+    }
+    if (staged >= 64) {
+      flush_out_rows<SH, K>(ost, staged, out, overflow);
+      staged = 0;
     }
   });
+  if (staged > 0) flush_out_rows<SH, K>(ost, staged, out, overflow);
   if (overflow) set_error(kp.err, PV_ERR_OUTPUT_OVERFLOW);
   __shared__ bool last;
   __syncthreads();
@@ -415,7 +488,10 @@ __global__ void __maxnreg__(128) k_project_compact(const __grid_constant__ KPara
 template <class SH, int K>
 static pv_status launch_proj_compact_k(const LaunchCfg& c, const KParams& kp, const ProjOut& out) {
   auto k = k_project_compact<SH, K>;
-  const size_t smem = static_cast<size_t>(c.block / 32) * queue_cap<K>() * 4;
+  const size_t smem = static_cast<size_t>(c.block / 32) * (queue_cap<K>() * 4 + out_stage_bytes<SH, K>());
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
+    return PV_ERR_UNSUPPORTED;
   const int grid = grid_for(c, reinterpret_cast<const void*>(k), smem, kp.n_items, c.block);
   if (grid <= 0) return PV_ERR_UNSUPPORTED;
   kmark(c);
@@ -523,7 +599,7 @@ static pv_status launch_agg(const LaunchCfg& c, const KParams& kp, const AggOut&
        {launch_agg_t<SH, false, true, 1>, launch_agg_t<SH, false, true, 2>, launch_agg_t<SH, false, true, 4>}},
       {{launch_agg_t<SH, true, false, 1>, launch_agg_t<SH, true, false, 2>, launch_agg_t<SH, true, false, 4>},
        {launch_agg_t<SH, true, true, 1>, launch_agg_t<SH, true, true, 2>, launch_agg_t<SH, true, true, 4>}}};
-  if (c.compact) return launch_agg_compact<SH>(c, kp, out);
+  if (c.compact) return c.compact_probes != 1 ? PV_ERR_UNSUPPORTED : launch_agg_compact<SH>(c, kp, out);
   const int ui = c.U == 1 ? 0 : c.U == 2 ? 1 : c.U == 4 ? 2 : -1;
   if (ui < 0) return PV_ERR_UNSUPPORTED;
   return tab[c.pred][c.chunk][ui](c, kp, out);
@@ -537,7 +613,7 @@ static pv_status launch_proj(const LaunchCfg& c, const KParams& kp, const ProjOu
        {launch_proj_t<SH, false, true, 1>, launch_proj_t<SH, false, true, 2>, launch_proj_t<SH, false, true, 4>}},
       {{launch_proj_t<SH, true, false, 1>, launch_proj_t<SH, true, false, 2>, launch_proj_t<SH, true, false, 4>},
        {launch_proj_t<SH, true, true, 1>, launch_proj_t<SH, true, true, 2>, launch_proj_t<SH, true, true, 4>}}};
-  if (c.compact) return launch_proj_compact<SH>(c, kp, out, exec);
+  if (c.compact) return c.compact_probes != 1 ? PV_ERR_UNSUPPORTED : launch_proj_compact<SH>(c, kp, out, exec);
   const int ui = c.U == 1 ? 0 : c.U == 2 ? 1 : c.U == 4 ? 2 : -1;
   if (ui < 0) return PV_ERR_UNSUPPORTED;
   return tab[c.pred][c.chunk][ui](c, kp, out, exec);

@@ -507,26 +507,67 @@ struct RefPay<J, Tm<Ts...>> : std::bool_constant<(RefPay<J, Ts>::value || ...)> 
 // projected values: slot S < 0 is the payload of probe -S - 1
 template <int J, int... S> struct RefPay<J, Proj<S...>> : std::bool_constant<((S == -J - 1) || ...)> {};
 
-// The row stage repeats the first probe only to bind its payload: when the
-// first operation was that probe and nothing reads its payload, it is skipped.
+// RefPay for a probe index known only in a constexpr loop.
 template <class SH>
-constexpr bool compact_skip_probe0() {
-  return SH::Where::N == 0 && !RefPay<0, typename SH::Key>::value && !RefPay<0, typename SH::Aggs>::value &&
-         !RefPay<0, typename SH::Proj>::value;
+struct RefPayAt {
+  static constexpr bool key(int j) {
+    return at<0>(j, [](auto J) { return RefPay<decltype(J)::value, typename SH::Key>::value; });
+  }
+  static constexpr bool aggs(int j) {
+    return at<0>(j, [](auto J) { return RefPay<decltype(J)::value, typename SH::Aggs>::value; });
+  }
+  static constexpr bool proj(int j) {
+    return at<0>(j, [](auto J) { return RefPay<decltype(J)::value, typename SH::Proj>::value; });
+  }
+  template <int I, class F>
+  static constexpr bool at(int j, F f) {
+    if constexpr (I >= PV_MAX_PROBES) {
+      return false;
+    } else {
+      return j == I ? f(std::integral_constant<int, I>{}) : at<I + 1>(j, f);
+    }
+  }
+};
+
+// Probes of the first stage: none after filters (the filters are the first
+// operation), else the first NF (variant compact_probes), which run over
+// whole items with their key columns read in full.
+template <class SH, int NF>
+constexpr int first_probes() {
+  return SH::Where::N > 0 ? 0 : (NF < SH::Probes::N ? NF : SH::Probes::N);
+}
+
+// The row stage repeats a first-stage probe only to bind its payload: when
+// nothing reads that payload, the probe is skipped.
+template <class SH, int NF, int J>
+constexpr bool compact_skip_probe() {
+  return J < first_probes<SH, NF>() && !RefPay<J, typename SH::Key>::value &&
+         !RefPay<J, typename SH::Aggs>::value && !RefPay<J, typename SH::Proj>::value;
+}
+
+// Key slots of the probes the row stage skips.
+template <class SH, int NF>
+constexpr uint32_t compact_skipped_slots() {
+  uint32_t m = 0;
+  for (int j = 0; j < SH::Probes::N && j < first_probes<SH, NF>(); ++j) {
+    const bool read = RefPayAt<SH>::key(j) || RefPayAt<SH>::aggs(j) || RefPayAt<SH>::proj(j);
+    if (!read) m |= 1u << SH::Probes::slot_of[j];
+  }
+  return m;
 }
 
 // Columns the sink reads for a queued row beyond the probe keys the row stage
-// loads (a skipped first probe's key column counts as not loaded).
-template <class SH>
+// loads (a skipped probe's key column counts as not loaded).
+template <class SH, int NF>
 constexpr uint32_t compact_row_slots() {
-  constexpr uint32_t probed = compact_skip_probe0<SH>() ? SH::Probes::slots & ~(1u << SH::Probes::slot_of[0])
-                                                        : SH::Probes::slots;
+  constexpr uint32_t probed = SH::Probes::slots & ~compact_skipped_slots<SH, NF>();
   return (SH::Key::slots | SH::Aggs::slots | SH::Proj::slots) & ~probed;
 }
 
-// First operation of an item (nvalid = 0 past the table): its filters, or
-// else its first probe; leaves the surviving rows in it.mask.
-template <class SH>
+// First stage of an item (nvalid = 0 past the table): its filters, or else
+// its first NF probes, the key column of each read for the whole item;
+// leaves the surviving rows in it.mask.
+template <class SH, int NF>
 __device__ __forceinline__ void compact_first(Item<SH>& it, const KParams& kp, int64_t item) {
   using W = typename SH::Where;
   using JP = typename SH::Probes;
@@ -537,17 +578,25 @@ __device__ __forceinline__ void compact_first(Item<SH>& it, const KParams& kp, i
     load_slots<SH, W::slots>(it, kp, item);
     static_for<W::N>([&](auto j) { it.mask &= pred_bits<SH, decltype(j)::value>(it, kp); });
   } else {
-    constexpr int S = JP::slot_of[0];
-    load_slots<SH, (1u << S)>(it, kp, item);
-    it.mask = probe_item(kp.probe[0], VGet<S>::get(it.v), it.mask, it.pay[0], false);
+    constexpr int NP = first_probes<SH, NF>();
+    static_for<NP>([&](auto j) {
+      constexpr int J = decltype(j)::value;
+      constexpr int S = JP::slot_of[J];
+      load_slots<SH, (1u << S)>(it, kp, item);
+    });
+    static_for<NP>([&](auto j) {
+      constexpr int J = decltype(j)::value;
+      constexpr int S = JP::slot_of[J];
+      it.mask = probe_item(kp.probe[J], VGet<S>::get(it.v), it.mask, it.pay[J], false);
+    });
   }
 }
 
 // K queued rows (has[k]: row k exists) as row 0 of K items: the probes stage
-// by stage for all K rows (the first probe again when it was the first
-// operation and its payload is read), then the loads of the columns the sink
-// reads.  ok[k] is false when a probe missed.
-template <class SH, int K>
+// by stage for all K rows (a first-stage probe again only when its payload is
+// read), then the loads of the columns the sink reads.  ok[k] is false when a
+// probe missed.
+template <class SH, int K, int NF>
 __device__ __forceinline__ void compact_load_rows(Item<SH> (&it)[K], bool (&ok)[K], const KParams& kp,
                                                   const uint32_t (&row)[K], const bool (&has)[K]) {
   using JP = typename SH::Probes;
@@ -561,9 +610,9 @@ __device__ __forceinline__ void compact_load_rows(Item<SH> (&it)[K], bool (&ok)[
     constexpr int J = decltype(j)::value;
     constexpr int S = JP::slot_of[J];
     using T = typename At<S, typename SH::Cols::L>::type::T;
-    if constexpr (J == 0 && compact_skip_probe0<SH>()) {
+    if constexpr (compact_skip_probe<SH, NF, J>()) {
 #pragma unroll
-      for (int k = 0; k < K; ++k) it[k].pay[J][0] = 0;  // the first operation was this probe, payload unread
+      for (int k = 0; k < K; ++k) it[k].pay[J][0] = 0;  // ran in the first stage, payload unread
     } else {
       T key[K];
 #pragma unroll
@@ -579,7 +628,7 @@ __device__ __forceinline__ void compact_load_rows(Item<SH> (&it)[K], bool (&ok)[
   });
   static_for<SH::Cols::N>([&](auto c) {
     constexpr int S = decltype(c)::value;
-    if constexpr ((compact_row_slots<SH>() >> S) & 1u) {
+    if constexpr ((compact_row_slots<SH, NF>() >> S) & 1u) {
       using T = typename At<S, typename SH::Cols::L>::type::T;
 #pragma unroll
       for (int k = 0; k < K; ++k)
@@ -596,7 +645,7 @@ __device__ __forceinline__ void compact_load_rows(Item<SH> (&it)[K], bool (&ok)[
 // the warp call this together.  ALL_LANES: every lane calls row_fn at every
 // drain, lanes without a row with has[] all false, so that row_fn may use warp
 // collectives; otherwise only lanes holding a row call it.
-template <class SH, int K, bool ALL_LANES = false, class F>
+template <class SH, int K, int NF, bool ALL_LANES = false, class F>
 __device__ __forceinline__ void for_rows_compacted(const KParams& kp, uint32_t* q, F&& row_fn) {
   constexpr int QC = queue_cap<K>();
   constexpr int KEEP = (QC - 32 * K + 31) / 32;  // entries a lane moves down after a drain
@@ -637,7 +686,7 @@ __device__ __forceinline__ void for_rows_compacted(const KParams& kp, uint32_t* 
   for (int64_t wb = t - lane; wb < kp.n_items; wb += T) {
     if (pf > 0) lp.issue(wb + pf * T, n_full);
     Item<SH> it;
-    compact_first(it, kp, wb + lane);
+    compact_first<SH, NF>(it, kp, wb + lane);
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const bool live = (it.mask >> r) & 1u;

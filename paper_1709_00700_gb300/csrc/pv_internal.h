@@ -31,6 +31,7 @@ struct LaunchCfg {
   bool compact;   // compacted: survivors of the first operation queued per warp (grouped pipelines)
   bool chunk;     // chunked access
   bool staged;    // TMA-staged access (grouped predicated pipelines)
+  int compact_probes;  // compacted: probes of the first stage (1 or 2)
   int* launches;  // incremented per kernel launch
   // optional per-kernel timing: called right before and right after a launch
   void (*mark)(void* timer, cudaStream_t s);

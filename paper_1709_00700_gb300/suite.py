@@ -77,11 +77,15 @@ GRIDS = {
              for bk, s, u in itertools.product(
                  ["perfect", "linear", "cuckoo"],
                  [dict(agg="local", ht="perfect"), dict(agg="global", ht="perfect"),
-                  dict(agg="local", ht="linear"), dict(agg="global", ht="linear")], [1, 2, 4])],
+                  dict(agg="local", ht="linear"), dict(agg="global", ht="linear")], [1, 2, 4])] +
+            # the first two probes over whole items (second key column read in full), then the queue
+            [dict(s, build=bk, pred="compacted", items_per_thread=u, block=256, prefetch=0, compact_probes=2)
+             for bk, s, u in itertools.product(
+                 ["perfect", "linear"], [dict(agg="local", ht="perfect"), dict(agg="global", ht="perfect")], [1, 2])],
 }
 
 
-_DEFAULTS = {"exec": "single", "threads_per_table": 0, "warp_agg": 0}
+_DEFAULTS = {"exec": "single", "threads_per_table": 0, "warp_agg": 0, "compact_probes": 1}
 
 
 def _normalize(grid: list) -> list:

@@ -646,6 +646,59 @@ def test_compacted_star_join(ctx, build_kind):
         _compacted(ctx, workloads.star_plan(th), s, pv.ht_variant(build_kind), step=7, min_ran=8)
 
 
+@pytest.mark.parametrize("build_kind", ["linear", "perfect"])
+def test_compacted_two_probe_first_stage(ctx, build_kind):
+    """compact_probes = 2: the first two probes run over whole items (both key
+    columns read in full) before the survivors are queued; the row stage
+    re-probes them only when their payloads are read (the three-probe join's
+    group keys), else skips them (the star join's first two dimensions)."""
+    s = _star_small(150_007, seed=35)
+    register(ctx, s)
+    htv = pv.ht_variant(build_kind)
+    for th in ({"d_a": 60, "d_b": 50, "d_c": 30, "d_d": 40}, {"d_a": 20, "d_b": 20, "d_c": 5, "d_d": 10}):
+        plan = workloads.star_plan(th)
+        w = want(plan, s)
+        ran = 0
+        for kw in COMPACT_VARIANTS[::5]:
+            got = run_or_skip(ctx, plan, pv.variant(**kw, compact_probes=2), htv)
+            if got is not None:
+                ran += 1
+                assert_same(got, w, ctxmsg=f"star {th} {kw}")
+        assert ran >= 8
+    s3 = datagen.star3_schema(120_011, seed=36)
+    register(ctx, s3)
+    for regions, years in (((2, 2), workloads.STAR3_YEARS), ((0, 4), (1993, 1996))):
+        plan = workloads.star3_plan(regions, years)
+        w = want(plan, s3)
+        for kw in COMPACT_VARIANTS[1::9]:
+            got = run_or_skip(ctx, plan, pv.variant(**kw, compact_probes=2), htv)
+            if got is not None:
+                assert_same(got, w, ctxmsg=f"star3 {regions} {kw}")
+    for n in (0, 1, 7, 129):  # empty and ragged fact tables
+        sn = _star_small(n, seed=n + 50)
+        register(ctx, sn)
+        plan = workloads.star_plan({"d_a": 60, "d_b": 50, "d_c": 30, "d_d": 40})
+        got = ctx.query(plan, pv.variant(agg="local", ht="perfect", pred="compacted", items_per_thread=2,
+                                         compact_probes=2), htv)
+        assert_same(got, want(plan, sn), ctxmsg=f"n={n}")
+
+
+def test_compacted_two_probe_first_stage_unsupported_forms(ctx):
+    kv = {"kv": datagen.table_keyval(1000, 10, seed=3)}
+    t = {"t": datagen.table_filter_agg(1000)}
+    register(ctx, kv)
+    register(ctx, t)
+    for plan in (workloads.keyval_plan(val_lt=5), workloads.filter_agg_plan(), workloads.filter_project_plan()):
+        with pytest.raises(pv.PVError) as e:  # filters first: no probe stage to widen
+            ctx.query(plan, pv.variant(pred="compacted", items_per_thread=1, compact_probes=2))
+        assert e.value.status == -2
+    for kw in (dict(pred="branch", compact_probes=2), dict(pred="compacted", compact_probes=3)):
+        with pytest.raises(pv.PVError) as e:
+            ctx.query(workloads.keyval_plan(val_lt=5), pv.variant(items_per_thread=1, **kw))
+        assert e.value.status == -1
+    ctx.sync()
+
+
 def test_compacted_min_max_join_and_ragged_tables(ctx):
     import json
     import os
@@ -1034,7 +1087,8 @@ def test_byte_coded_perfect_tables(ctx):
 @pytest.mark.parametrize("n", [0, 5, 4_099, 300_007])
 def test_compacted_projections(ctx, n):
     """Single-pass PROJECT in compacted mode: the first operation's survivors
-    queued per warp, one or two per lane, output positions reserved per warp.
+    queued per warp, one or two per lane, surviving rows staged per warp in
+    shared memory and written out 64 or more at a time.
     Filter-first and probe-first plans, projecting fact columns and probe
     payloads, against the oracle as multisets; an output too small is
     reported."""
@@ -1044,7 +1098,7 @@ def test_compacted_projections(ctx, n):
                  {"fact": "t", "filters": [["a", "lt", 30]], "project": ["b", "price"]}):
         w = want(plan, t)
         for kw in (dict(items_per_thread=1, block=256), dict(items_per_thread=2, block=512, prefetch=1),
-                   dict(items_per_thread=2, block=64, grid_mult=1)):
+                   dict(items_per_thread=2, block=64, grid_mult=1), dict(items_per_thread=2, block=1024)):
             got = ctx.query(plan, pv.variant(pred="compacted", exec="single", **kw))
             assert_same(got, w, ordered=False, ctxmsg=f"{plan['filters']} {kw}")
     if n:
