@@ -196,6 +196,11 @@ typedef struct {
                                 With 2, the second probe's key column is read in full instead of being
                                 gathered for the queued rows; ungrouped pipelines and pipelines with
                                 filters or one probe return PV_ERR_UNSUPPORTED for 2. */
+  int32_t first_items;       /* PV_COMPACTED: 4-row items a lane takes through the first stage per loop trip,
+                                1 (0 = 1) or 2; with 2 the loads of both items are in flight together before
+                                either is filtered and queued.  Compiled for pipelines whose first operation
+                                is a filter; probe-first pipelines return PV_ERR_UNSUPPORTED for 2, and 2
+                                without PV_COMPACTED is PV_ERR_INVALID_ARG. */
   uint64_t seed;             /* aggregation hash seeds */
 } pv_variant;
 

@@ -34,7 +34,8 @@ PLAN_FEATURES = ("log_rows", "sel", "log_sel", "log_groups", "log_groups_per_row
                  "log_sel_after_first")
 VARIANT_FEATURES = ("multi", "local", "ht_linear", "ht_cuckoo", "ht_perfect", "multshift", "predicated",
                     "chunked", "log_block", "grid_mult", "unroll", "private_tables", "prefetch", "build_linear",
-                    "build_cuckoo", "build_perfect", "warp_agg", "compacted", "cluster", "compact_probes2")
+                    "build_cuckoo", "build_perfect", "warp_agg", "compacted", "cluster", "compact_probes2",
+                    "first_items2")
 N_FEATURES = len(PLAN_FEATURES) + len(VARIANT_FEATURES)
 
 
@@ -77,7 +78,7 @@ def variant_vector(v: dict) -> list:
             float(v.get("threads_per_table", 0) == 1), float(v.get("prefetch", 0)), float(b == "linear"),
             float(b == "cuckoo"), float(b == "perfect"), float(v.get("warp_agg", 0)),
             float(v.get("pred") == "compacted"), float(v.get("agg") == "cluster"),
-            float(v.get("compact_probes", 1) == 2)]
+            float(v.get("compact_probes", 1) == 2), float(v.get("first_items", 1) == 2)]
 
 
 def features(stats: dict, variant: dict) -> np.ndarray:

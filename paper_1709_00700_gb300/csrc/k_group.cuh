@@ -890,7 +890,7 @@ __global__ void __maxnreg__((GroupRegs<SH, Sink, true>::value)) k_group_staged(
 // survivors of the first stage (the filters, else the first NF probes) per
 // warp; each queued row runs the other probes, the sink's column loads and
 // the sink, K rows per lane.
-template <class SH, class Sink, int K, int NF>
+template <class SH, class Sink, int K, int NF, int FI>
 __global__ void __maxnreg__((GroupRegs<SH, Sink, false>::value)) k_group_compact(
     const __grid_constant__ KParams kp, const __grid_constant__ GroupDesc gd, const __grid_constant__ GroupOut g) {
   extern __shared__ unsigned long long smem[];
@@ -899,7 +899,7 @@ __global__ void __maxnreg__((GroupRegs<SH, Sink, false>::value)) k_group_compact
   if (blockIdx.x == 0 && threadIdx.x == 0) *g.out_count = 0;  // extraction runs after this kernel
   Sink sink(gd, g, kp.err, smem + nwarps * queue_cap<K>() / 2);  // the queues, 4 bytes an entry
   sink.init();
-  for_rows_compacted<SH, K, NF>(kp, q, [&](const uint32_t (&rows)[K], const bool (&has)[K]) {
+  for_rows_compacted<SH, K, NF, false, FI>(kp, q, [&](const uint32_t (&rows)[K], const bool (&has)[K]) {
     Item<SH> it[K];
     bool ok[K];
     compact_load_rows<SH, K, NF>(it, ok, kp, rows, has);
@@ -971,19 +971,30 @@ static pv_status launch_k(const LaunchCfg& c, K k, const KParams& kp, const Grou
   return cudaGetLastError() == cudaSuccess ? PV_OK : PV_ERR_CUDA;
 }
 
-template <class SH, template <class> class SinkT, int NF>
-static pv_status run_group_compact_nf(const LaunchCfg& c, const KParams& kp, const GroupDesc& gd, const GroupOut& g,
+template <class SH, template <class> class SinkT, int NF, int FI>
+static pv_status run_group_compact_fi(const LaunchCfg& c, const KParams& kp, const GroupDesc& gd, const GroupOut& g,
                                       size_t sink_smem) {
   if (c.U == 4) {
     const size_t smem = static_cast<size_t>(c.block / 32) * queue_cap<4>() * 4 + sink_smem;
-    return launch_k(c, k_group_compact<SH, SinkT<SH>, 4, NF>, kp, gd, g, smem, 1);
+    return launch_k(c, k_group_compact<SH, SinkT<SH>, 4, NF, FI>, kp, gd, g, smem, FI);
   }
   if (c.U == 2) {
     const size_t smem = static_cast<size_t>(c.block / 32) * queue_cap<2>() * 4 + sink_smem;
-    return launch_k(c, k_group_compact<SH, SinkT<SH>, 2, NF>, kp, gd, g, smem, 1);
+    return launch_k(c, k_group_compact<SH, SinkT<SH>, 2, NF, FI>, kp, gd, g, smem, FI);
   }
   const size_t smem = static_cast<size_t>(c.block / 32) * queue_cap<1>() * 4 + sink_smem;
-  return launch_k(c, k_group_compact<SH, SinkT<SH>, 1, NF>, kp, gd, g, smem, 1);
+  return launch_k(c, k_group_compact<SH, SinkT<SH>, 1, NF, FI>, kp, gd, g, smem, FI);
+}
+
+// first_items 2: filter-first pipelines only (first_items_max).
+template <class SH, template <class> class SinkT, int NF>
+static pv_status run_group_compact_nf(const LaunchCfg& c, const KParams& kp, const GroupDesc& gd, const GroupOut& g,
+                                      size_t sink_smem) {
+  if (c.first_items > first_items_max<SH>()) return PV_ERR_UNSUPPORTED;
+  if constexpr (first_items_max<SH>() == 2) {
+    if (c.first_items == 2) return run_group_compact_fi<SH, SinkT, NF, 2>(c, kp, gd, g, sink_smem);
+  }
+  return run_group_compact_fi<SH, SinkT, NF, 1>(c, kp, gd, g, sink_smem);
 }
 
 template <class SH, template <class> class SinkT>

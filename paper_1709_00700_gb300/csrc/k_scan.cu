@@ -338,7 +338,7 @@ __global__ void __maxnreg__(128) k_project_scatter(const __grid_constant__ KPara
 // ---------------------------------------------------------------------------
 // Compacted execution of an ungrouped aggregation: the rows that survive the
 // first operation are queued per warp and accumulated one per lane.
-template <class SH, int K>
+template <class SH, int K, int FI>
 __global__ void __maxnreg__(128) k_aggregate_compact(const __grid_constant__ KParams kp,
                                                      const __grid_constant__ AggOut out) {
   using A = typename SH::Aggs;
@@ -347,7 +347,7 @@ __global__ void __maxnreg__(128) k_aggregate_compact(const __grid_constant__ KPa
   uint64_t acc[NA + 1];
 #pragma unroll
   for (int a = 0; a <= NA; ++a) acc[a] = 0;
-  for_rows_compacted<SH, K, 1>(kp, qmem + (threadIdx.x >> 5) * queue_cap<K>(),
+  for_rows_compacted<SH, K, 1, false, FI>(kp, qmem + (threadIdx.x >> 5) * queue_cap<K>(),
                             [&](const uint32_t (&rows)[K], const bool (&has)[K]) {
     Item<SH> it[K];
     bool ok[K];
@@ -444,7 +444,7 @@ __device__ __forceinline__ void flush_out_rows(const char* st, int n, const Proj
 // writes them out coalesced: one atomic per 64 to 127 output rows, where one
 // per drain put the whole grid on one counter.  Output order is arbitrary, as
 // for the other single-pass projection.
-template <class SH, int K>
+template <class SH, int K, int FI>
 __global__ void __maxnreg__(128) k_project_compact(const __grid_constant__ KParams kp,
                                                    const __grid_constant__ ProjOut out) {
   extern __shared__ uint32_t qmem[];
@@ -452,7 +452,7 @@ __global__ void __maxnreg__(128) k_project_compact(const __grid_constant__ KPara
   char* ost = reinterpret_cast<char*>(qmem + nwarps * queue_cap<K>()) + warp * out_stage_bytes<SH, K>();
   bool overflow = false;
   int staged = 0;  // warp-uniform
-  for_rows_compacted<SH, K, 1, true>(kp, qmem + warp * queue_cap<K>(),
+  for_rows_compacted<SH, K, 1, true, FI>(kp, qmem + warp * queue_cap<K>(),
                                      [&](const uint32_t (&rows)[K], const bool (&has)[K]) {
     Item<SH> it[K];
     bool ok[K];
@@ -487,7 +487,7 @@ __global__ void __maxnreg__(128) k_project_compact(const __grid_constant__ KPara
 
 template <class SH, int K>
 static pv_status launch_proj_compact_k(const LaunchCfg& c, const KParams& kp, const ProjOut& out) {
-  auto k = k_project_compact<SH, K>;
+  auto k = c.first_items == 2 ? k_project_compact<SH, K, first_items_max<SH>()> : k_project_compact<SH, K, 1>;
   const size_t smem = static_cast<size_t>(c.block / 32) * (queue_cap<K>() * 4 + out_stage_bytes<SH, K>());
   if (smem > 48 * 1024 &&
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
@@ -508,7 +508,7 @@ static pv_status launch_proj_compact(const LaunchCfg& c, const KParams& kp, cons
   } else {
     // single pass only: the queues reorder rows, and multi-pass output keeps input order
     if (exec != PV_EXEC_SINGLE_PASS || c.chunk || (c.U != 1 && c.U != 2) ||
-        kp.n_rows > static_cast<int64_t>(UINT32_MAX))
+        kp.n_rows > static_cast<int64_t>(UINT32_MAX) || c.first_items > first_items_max<SH>())
       return PV_ERR_UNSUPPORTED;
     return c.U == 2 ? launch_proj_compact_k<SH, 2>(c, kp, out) : launch_proj_compact_k<SH, 1>(c, kp, out);
   }
@@ -516,7 +516,7 @@ static pv_status launch_proj_compact(const LaunchCfg& c, const KParams& kp, cons
 
 template <class SH, int K>
 static pv_status launch_agg_compact_k(const LaunchCfg& c, const KParams& kp, const AggOut& out) {
-  auto k = k_aggregate_compact<SH, K>;
+  auto k = c.first_items == 2 ? k_aggregate_compact<SH, K, first_items_max<SH>()> : k_aggregate_compact<SH, K, 1>;
   const size_t smem = static_cast<size_t>(c.block / 32) * queue_cap<K>() * 4;
   const int grid = grid_for(c, reinterpret_cast<const void*>(k), smem, kp.n_items, c.block);
   if (grid <= 0) return PV_ERR_UNSUPPORTED;
@@ -533,7 +533,9 @@ static pv_status launch_agg_compact(const LaunchCfg& c, const KParams& kp, const
     return PV_ERR_UNSUPPORTED;  // nothing to compact on
   } else {
     // items_per_thread: queued rows a lane takes through the row stage at once
-    if (c.chunk || (c.U != 1 && c.U != 2) || kp.n_rows > static_cast<int64_t>(UINT32_MAX)) return PV_ERR_UNSUPPORTED;
+    if (c.chunk || (c.U != 1 && c.U != 2) || kp.n_rows > static_cast<int64_t>(UINT32_MAX) ||
+        c.first_items > first_items_max<SH>())
+      return PV_ERR_UNSUPPORTED;
     return c.U == 2 ? launch_agg_compact_k<SH, 2>(c, kp, out) : launch_agg_compact_k<SH, 1>(c, kp, out);
   }
 }

@@ -461,6 +461,9 @@ static pv_status resolve_launch(pv_ctx* c, const pv_variant& v, LaunchCfg& L) {
   if (v.compact_probes < 0 || v.compact_probes > 2) return fail(c, PV_ERR_INVALID_ARG, "compact_probes must be 0..2");
   L.compact_probes = v.compact_probes ? v.compact_probes : 1;
   if (L.compact_probes != 1 && !L.compact) return fail(c, PV_ERR_INVALID_ARG, "compact_probes needs pred = compacted");
+  if (v.first_items < 0 || v.first_items > 2) return fail(c, PV_ERR_INVALID_ARG, "first_items must be 0..2");
+  L.first_items = v.first_items ? v.first_items : 1;
+  if (L.first_items != 1 && !L.compact) return fail(c, PV_ERR_INVALID_ARG, "first_items needs pred = compacted");
   L.launches = &c->launches;
   if (c->ktime && !c->capturing) {
     L.mark = ktimer_mark;

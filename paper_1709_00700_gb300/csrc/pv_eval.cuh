@@ -565,10 +565,11 @@ constexpr uint32_t compact_row_slots() {
 }
 
 // First stage of an item (nvalid = 0 past the table): its filters, or else
-// its first NF probes, the key column of each read for the whole item;
-// leaves the surviving rows in it.mask.
+// its first NF probes, the key column of each read for the whole item
+// (compact_first_load); then the filters or probes leave the surviving rows in
+// it.mask (compact_first_eval).
 template <class SH, int NF>
-__device__ __forceinline__ void compact_first(Item<SH>& it, const KParams& kp, int64_t item) {
+__device__ __forceinline__ void compact_first_load(Item<SH>& it, const KParams& kp, int64_t item) {
   using W = typename SH::Where;
   using JP = typename SH::Probes;
   const int64_t left = kp.n_rows - item * 4;
@@ -576,14 +577,22 @@ __device__ __forceinline__ void compact_first(Item<SH>& it, const KParams& kp, i
   it.mask = (1u << it.nvalid) - 1u;
   if constexpr (W::N > 0) {
     load_slots<SH, W::slots>(it, kp, item);
-    static_for<W::N>([&](auto j) { it.mask &= pred_bits<SH, decltype(j)::value>(it, kp); });
   } else {
     constexpr int NP = first_probes<SH, NF>();
     static_for<NP>([&](auto j) {
-      constexpr int J = decltype(j)::value;
-      constexpr int S = JP::slot_of[J];
+      constexpr int S = JP::slot_of[decltype(j)::value];
       load_slots<SH, (1u << S)>(it, kp, item);
     });
+  }
+}
+template <class SH, int NF>
+__device__ __forceinline__ void compact_first_eval(Item<SH>& it, const KParams& kp) {
+  using W = typename SH::Where;
+  using JP = typename SH::Probes;
+  if constexpr (W::N > 0) {
+    static_for<W::N>([&](auto j) { it.mask &= pred_bits<SH, decltype(j)::value>(it, kp); });
+  } else {
+    constexpr int NP = first_probes<SH, NF>();
     static_for<NP>([&](auto j) {
       constexpr int J = decltype(j)::value;
       constexpr int S = JP::slot_of[J];
@@ -637,6 +646,13 @@ __device__ __forceinline__ void compact_load_rows(Item<SH> (&it)[K], bool (&ok)[
   });
 }
 
+// Largest first_items compiled for a shape: 2 for pipelines whose first
+// operation is a filter, 1 for probe-first ones (two items in flight were
+// measured slower there: the probes' table lookups, not the key loads, bound
+// them).
+template <class SH>
+constexpr int first_items_max() { return SH::Where::N > 0 ? 2 : 1; }
+
 // The item loop of compacted execution (grid-stride, every lane of a warp
 // runs every trip): the first operation over whole items, its surviving rows
 // appended to the warp's queue q (queue_cap<K>() entries in shared memory),
@@ -644,8 +660,12 @@ __device__ __forceinline__ void compact_load_rows(Item<SH> (&it)[K], bool (&ok)[
 // takes entries l, l + 32, ...); the rows left at the end follow.  All lanes of
 // the warp call this together.  ALL_LANES: every lane calls row_fn at every
 // drain, lanes without a row with has[] all false, so that row_fn may use warp
-// collectives; otherwise only lanes holding a row call it.
-template <class SH, int K, int NF, bool ALL_LANES = false, class F>
+// collectives; otherwise only lanes holding a row call it.  FI (variant
+// first_items): items a lane takes through the first stage per trip, their
+// loads issued together before the first is evaluated; each item's survivors
+// are appended and drained before the next, so the queue stays within
+// queue_cap<K>().
+template <class SH, int K, int NF, bool ALL_LANES = false, int FI = 1, class F>
 __device__ __forceinline__ void for_rows_compacted(const KParams& kp, uint32_t* q, F&& row_fn) {
   constexpr int QC = queue_cap<K>();
   constexpr int KEEP = (QC - 32 * K + 31) / 32;  // entries a lane moves down after a drain
@@ -682,20 +702,29 @@ __device__ __forceinline__ void for_rows_compacted(const KParams& kp, uint32_t* 
   const int64_t n_full = kp.n_rows >> 2;
   const int pf = kp.prefetch;
   const LanePrefetch<SH, first_stage_slots<SH>()> lp(kp, lane);
-  for (int d = 1; d < pf; ++d) lp.issue((t - lane) + d * T, n_full);
-  for (int64_t wb = t - lane; wb < kp.n_items; wb += T) {
-    if (pf > 0) lp.issue(wb + pf * T, n_full);
-    Item<SH> it;
-    compact_first<SH, NF>(it, kp, wb + lane);
+  // warp chunks (units of T items) pf trips ahead; trip 0 reads chunks 0 .. FI - 1
+  for (int d = FI; d < pf * FI; ++d) lp.issue((t - lane) + d * T, n_full);
+  for (int64_t wb = t - lane; wb < kp.n_items; wb += FI * T) {
+    if (pf > 0) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const bool live = (it.mask >> r) & 1u;
-      const uint32_t b = __ballot_sync(0xffffffffu, live);
-      if (live) q[qlen + __popc(b & lt)] = static_cast<uint32_t>((wb + lane) * 4 + r);
-      qlen += __popc(b);
+      for (int f = 0; f < FI; ++f) lp.issue(wb + static_cast<int64_t>(pf * FI + f) * T, n_full);
     }
-    __syncwarp();
-    while (qlen >= 32 * K) drain(32 * K);
+    Item<SH> it[FI];
+#pragma unroll
+    for (int f = 0; f < FI; ++f) compact_first_load<SH, NF>(it[f], kp, wb + f * T + lane);
+#pragma unroll
+    for (int f = 0; f < FI; ++f) {
+      compact_first_eval<SH, NF>(it[f], kp);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const bool live = (it[f].mask >> r) & 1u;
+        const uint32_t b = __ballot_sync(0xffffffffu, live);
+        if (live) q[qlen + __popc(b & lt)] = static_cast<uint32_t>((wb + f * T + lane) * 4 + r);
+        qlen += __popc(b);
+      }
+      __syncwarp();
+      while (qlen >= 32 * K) drain(32 * K);
+    }
   }
   if (qlen > 0) drain(qlen);
 }

@@ -32,6 +32,7 @@ struct LaunchCfg {
   bool chunk;     // chunked access
   bool staged;    // TMA-staged access (grouped predicated pipelines)
   int compact_probes;  // compacted: probes of the first stage (1 or 2)
+  int first_items;     // compacted: items a lane takes through the first stage per trip (1 or 2)
   int* launches;  // incremented per kernel launch
   // optional per-kernel timing: called right before and right after a launch
   void (*mark)(void* timer, cudaStream_t s);

@@ -82,7 +82,8 @@ class pv_variant(ctypes.Structure):
                 ("block", ctypes.c_int32), ("grid_mult", ctypes.c_int32),
                 ("items_per_thread", ctypes.c_int32), ("threads_per_table", ctypes.c_int32),
                 ("cuckoo_k", ctypes.c_int32), ("prefetch", ctypes.c_int32), ("warp_agg", ctypes.c_int32),
-                ("interp", ctypes.c_int32), ("compact_probes", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("interp", ctypes.c_int32), ("compact_probes", ctypes.c_int32), ("first_items", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -179,14 +180,16 @@ class PVError(RuntimeError):
 
 def variant(exec="single", agg="local", pred="branch", access="grid", ht="linear", hash="murmur",
             block=256, grid_mult=0, items_per_thread=2, threads_per_table=0, cuckoo_k=3, seed=0,
-            prefetch=0, warp_agg=0, interp=0, compact_probes=1) -> pv_variant:
+            prefetch=0, warp_agg=0, interp=0, compact_probes=1, first_items=1) -> pv_variant:
     """A pv_variant from readable names (the variant dimensions of Section 3.3).
     interp=1 runs the pipeline on the generic kernels even when a compiled
     shape matches it.  compact_probes (compacted mode): probes run over whole
-    items before the survivors are queued."""
+    items before the survivors are queued.  first_items (compacted mode):
+    items a lane takes through the first stage per trip, their loads in
+    flight together."""
     return pv_variant(EXEC[exec], AGG[agg], PRED[pred], ACCESS[access], HT[ht], HASH[hash], block, grid_mult,
                       items_per_thread, threads_per_table, cuckoo_k, prefetch, warp_agg, interp, compact_probes,
-                      seed)
+                      first_items, seed)
 
 
 def ht_variant(kind="linear", hash="murmur", cuckoo_k=3, max_evictions=0, load_factor=0.5, seed=0) -> pv_ht_variant:

@@ -37,12 +37,17 @@ GRIDS = {
                          for p, a, u, b, f in itertools.product(["branch", "predicated"], ["grid", "chunked"],
                                                                 [1, 4], [256, 512], [0, 1])] +
                         [dict(pred="compacted", access="grid", items_per_thread=u, block=b, prefetch=f)
-                         for u, b, f in itertools.product([1, 2], [256, 512], [0, 1])],
+                         for u, b, f in itertools.product([1, 2], [256, 512], [0, 1])] +
+                        # two items per lane through the first stage, their loads in flight together
+                        [dict(pred="compacted", access="grid", items_per_thread=u, block=b, prefetch=0, first_items=2)
+                         for u, b in itertools.product([1, 2], [256, 512])],
     "filter_project": [dict(exec=e, pred=p, access=a, items_per_thread=u, block=256, prefetch=f)
                        for e, p, a, u, f in itertools.product(["single", "multi"], ["branch", "predicated"],
                                                               ["grid", "chunked"], [1, 4], [0, 1])] +
                       [dict(exec="single", pred="compacted", access="grid", items_per_thread=u, block=256, prefetch=f)
-                       for u, f in itertools.product([1, 2], [0, 1])],
+                       for u, f in itertools.product([1, 2], [0, 1])] +
+                      [dict(exec="single", pred="compacted", access="grid", items_per_thread=u, block=256, prefetch=0,
+                            first_items=2) for u in (1, 2)],
     "grouped": [dict(s, pred=p, items_per_thread=1, block=256, prefetch=f)
                 for s, p, f in itertools.product(
                     [dict(agg="local", ht="perfect"), dict(agg="local", ht="perfect", threads_per_table=1),
@@ -60,6 +65,9 @@ GRIDS = {
                [dict(s, pred="compacted", items_per_thread=u, block=256, prefetch=0)
                 for s, u in itertools.product([dict(agg="local", ht="perfect"), dict(agg="global", ht="perfect"),
                                                dict(agg="local", ht="linear"), dict(agg="global", ht="linear")],
+                                              [1, 2])] +
+               [dict(s, pred="compacted", items_per_thread=u, block=256, prefetch=0, first_items=2)
+                for s, u in itertools.product([dict(agg="local", ht="perfect"), dict(agg="global", ht="perfect")],
                                               [1, 2])] +
                # perfect array in the distributed shared memory of a cluster of 2 to 16 CTAs
                [dict(agg="cluster", ht="perfect", pred="branch", items_per_thread=1, block=512, prefetch=0,
@@ -85,7 +93,7 @@ GRIDS = {
 }
 
 
-_DEFAULTS = {"exec": "single", "threads_per_table": 0, "warp_agg": 0, "compact_probes": 1}
+_DEFAULTS = {"exec": "single", "threads_per_table": 0, "warp_agg": 0, "compact_probes": 1, "first_items": 1}
 
 
 def _normalize(grid: list) -> list:

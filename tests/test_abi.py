@@ -43,7 +43,7 @@ def test_binding_structs_match_header_sizes():
     assert ctypes.sizeof(pv.pv_pred) == 24
     assert ctypes.sizeof(pv.pv_term) == 24
     assert ctypes.sizeof(pv.pv_agg) == 8 + 3 * 24
-    assert ctypes.sizeof(pv.pv_variant) == 15 * 4 + 4 + 8  # 15 int32 fields, padding, the uint64 seed
+    assert ctypes.sizeof(pv.pv_variant) == 16 * 4 + 8  # 16 int32 fields, the uint64 seed
     assert ctypes.sizeof(pv.pv_ht_variant) == 16 + 8 + 8
 
 

@@ -721,6 +721,67 @@ def test_compacted_min_max_join_and_ragged_tables(ctx):
             assert_same(got, w, ctxmsg=f"n={n} {kw}")
 
 
+@pytest.mark.parametrize("n", [0, 1, 5, 4_097, 200_003])
+def test_compacted_two_first_stage_items(ctx, n):
+    """first_items = 2: a lane loads two items' filter columns per trip before
+    filtering and queueing either.  Ungrouped aggregates, projections (fact
+    columns and a probe payload behind a filter), the grouped filter-first
+    pipelines (thread-private, CTA-local and global tables, 1, 2 and 4 queued
+    rows per lane), empty and ragged tables, against the oracle; probe-first
+    pipelines are PV_ERR_UNSUPPORTED and first_items outside compacted mode an
+    invalid argument."""
+    t = {"t": datagen.table_filter_agg(n, seed=n + 71)}
+    register(ctx, t)
+    for plan in (workloads.filter_agg_plan(), workloads.filter_agg_plan(a_lt=100, b_lo=0, b_hi=99),
+                 workloads.filter_agg_plan(a_lt=0)):
+        w = want(plan, t)
+        for kw in (dict(items_per_thread=1, block=256), dict(items_per_thread=2, block=512),
+                   dict(items_per_thread=2, block=64, grid_mult=1, prefetch=1), dict(items_per_thread=1, block=1024)):
+            got = ctx.query(plan, pv.variant(pred="compacted", first_items=2, **kw))
+            assert_same(got, w, ctxmsg=f"{plan['filters']} {kw}")
+    for plan in (workloads.filter_project_plan(), workloads.filter_project_plan(a_lt=100, b_lo=0, b_hi=99)):
+        w = want(plan, t)
+        for kw in (dict(items_per_thread=1, block=256), dict(items_per_thread=2, block=512, prefetch=1)):
+            got = ctx.query(plan, pv.variant(pred="compacted", exec="single", first_items=2, **kw))
+            assert_same(got, w, ordered=False, ctxmsg=f"{plan['filters']} {kw}")
+    li = {"li": datagen.table_lowcard_groups(n, seed=n + 72)}
+    register(ctx, li)
+    plan = workloads.lowcard_plan(day_hi=datagen.DAY0 + 300)
+    w = want(plan, li)
+    for kw in COMPACT_VARIANTS[::7]:
+        got = run_or_skip(ctx, plan, pv.variant(**kw, first_items=2))
+        if got is not None:
+            assert_same(got, w, ctxmsg=f"lowcard {kw}")
+    kv = {"kv": datagen.table_keyval(n, 1000, "zipf", seed=n + 73)}
+    register(ctx, kv)
+    plan = workloads.keyval_plan(val_lt=30_000)
+    w = want(plan, kv)
+    for kw in COMPACT_VARIANTS[3::11]:
+        got = run_or_skip(ctx, plan, pv.variant(**kw, first_items=2))
+        if got is not None:
+            assert_same(got, w, ctxmsg=f"keyval {kw}")
+    if n:
+        s = _star_small(n, seed=n + 74)
+        register(ctx, s)
+        proj = {"fact": "fact", "filters": [["fk_a", "lt", 1000]],
+                "builds": [{"table": "d_b", "key": "key", "filters": [["f", "lt", 40]], "payload": ["g"]}],
+                "probes": [{"build": 0, "fk": "fk_b"}], "project": [["payload", 0, 0], "revenue"]}
+        for build in ("perfect", "linear"):
+            got = ctx.query(proj, pv.variant(pred="compacted", exec="single", items_per_thread=2, first_items=2),
+                            pv.ht_variant(build))
+            assert_same(got, want(proj, s), ordered=False, ctxmsg=f"filtered join projection {build}")
+        with pytest.raises(pv.PVError) as e:  # probe-first: one item per trip only
+            ctx.query(workloads.star_plan(), pv.variant(agg="local", ht="perfect", pred="compacted",
+                                                        items_per_thread=2, first_items=2))
+        assert e.value.status == -2
+    for kw in (dict(pred="branch", first_items=2), dict(pred="predicated", first_items=2),
+               dict(pred="compacted", first_items=3)):
+        with pytest.raises(pv.PVError) as e:
+            ctx.query(workloads.filter_agg_plan(), pv.variant(items_per_thread=1, **kw))
+        assert e.value.status == -1, kw
+    ctx.sync()
+
+
 def test_compacted_is_unsupported_where_it_does_not_apply(ctx):
     kv = {"kv": datagen.table_keyval(1000, 10, seed=3)}
     register(ctx, kv)

@@ -27,4 +27,5 @@ def test_grids_have_uniform_keys_and_algorithm1_runs_on_lookups():
                    + 0.1 * (v["items_per_thread"] == 1) + 0.01 * (v["block"] == 256) + 0.001 * v["prefetch"]
                    for v in grid} for i in range(3)}
     v = suite.algorithm1_config(train, timings, grid)
-    assert v == {"pred": "branch", "access": "grid", "items_per_thread": 4, "block": 512, "prefetch": 0}
+    assert v == {"pred": "branch", "access": "grid", "items_per_thread": 4, "block": 512, "prefetch": 0,
+                 "first_items": 1}
