@@ -494,6 +494,7 @@ def run_pv(args):
     rows = args.rows or w["rows"]
     tables, plan = make_tables(args.workload, rows, args.groups, args.dist)
     ctx = pv.Context(local)
+    ctx.set_l2_fetch_bytes(args.l2_fetch_bytes)
     dev = {t: {c: torch.from_numpy(np.ascontiguousarray(v)).cuda(local) for c, v in cols.items()}
            for t, cols in tables.items()}
     for t, cols in dev.items():
@@ -598,7 +599,8 @@ def run_pv(args):
                    "l2": ("hot: no flush between steps, the inputs stay in L2 (hot-L2 numbers)" if args.hot_l2 else
                           "flushed (2x L2 write, then discard) before every step, outside the timed events"),
                    "step": "one CUDA graph replay of the pipeline" if args.graph else "one pv_rerun of the pipeline",
-                   "seed": datagen.DEFAULT_SEED, "parallelism": f"replicas x{world}"},
+                   "seed": datagen.DEFAULT_SEED, "parallelism": f"replicas x{world}",
+                   "l2_fetch_bytes": args.l2_fetch_bytes},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": ncu_traffic(args.workload),
                      "kernel_index": dom, "kernel_ms": dom_ms, "algorithmic_bytes": alg_bytes,
@@ -736,6 +738,7 @@ def run_pv_chain(args):
     rows = args.rows or w["rows"]
     tables, chain = datagen.tpch_schema(rows), workloads.q5_chain()
     ctx = pv.Context(local)
+    ctx.set_l2_fetch_bytes(args.l2_fetch_bytes)
     dev = {t: {c: torch.from_numpy(np.ascontiguousarray(v)).cuda(local) for c, v in cols.items()}
            for t, cols in tables.items()}
     for t, cols in dev.items():
@@ -855,7 +858,8 @@ def run_pv_chain(args):
         "config": {"workload": describe("q5", rows), "rows": rows, "variants": variants, "build": args.build_ht, "tuning": tuning,
                    "l2": ("hot: no flush between steps" if args.hot_l2 else
                           "flushed (2x L2 write, then discard) before every step, outside the timed events"),
-                   "seed": datagen.DEFAULT_SEED, "parallelism": f"replicas x{world}"},
+                   "seed": datagen.DEFAULT_SEED, "parallelism": f"replicas x{world}",
+                   "l2_fetch_bytes": args.l2_fetch_bytes},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "kernel": "line-item pipeline (step nat), its longest kernel",
                      "kernel_ms": dom_ms, "algorithmic_bytes": alg_bytes, "peak_source": f"{peak_kind} hbm_gbs",
@@ -912,6 +916,8 @@ def main():
     ap.add_argument("--hot-l2", action="store_true",
                     help="no L2 flush between steps (hot-L2 numbers, labelled as such)")
     ap.add_argument("--cpu-threads", type=int, default=0, help="oracle threads (0 = all host cores)")
+    ap.add_argument("--l2-fetch-bytes", type=int, default=32, choices=[0, 32, 64, 128],
+                    help="L2 fetch granularity of the CUDA context (pv_set_l2_fetch_bytes; 0 = driver's choice)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -843,6 +843,19 @@ pv_status pv_device_info(pv_ctx* c, int32_t* sm_count, int64_t* l2_bytes) {
   return PV_OK;
 }
 
+pv_status pv_set_l2_fetch_bytes(pv_ctx* c, int32_t bytes, int32_t* previous) {
+  if (!c) return PV_ERR_INVALID_ARG;
+  if (bytes != 0 && bytes != 32 && bytes != 64 && bytes != 128)
+    return fail(c, PV_ERR_INVALID_ARG, "L2 fetch bytes must be 0, 32, 64 or 128");
+  if (c->capturing) return fail(c, PV_ERR_INVALID_ARG, "pv_set_l2_fetch_bytes cannot be captured");
+  PV_CUDA(c, cudaSetDevice(c->device));
+  size_t old = 0;
+  PV_CUDA(c, cudaDeviceGetLimit(&old, cudaLimitMaxL2FetchGranularity));
+  PV_CUDA(c, cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, static_cast<size_t>(bytes)));
+  if (previous) *previous = static_cast<int32_t>(old);
+  return PV_OK;
+}
+
 pv_status pv_register_column(pv_ctx* c, const char* table, const char* name, int32_t type,
                              const void* dev_ptr, int64_t n_rows, pv_col* out) {
   if (!c || !out) return PV_ERR_INVALID_ARG;

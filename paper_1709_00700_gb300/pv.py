@@ -95,6 +95,7 @@ _SIGS = {
     "pv_destroy": (ctypes.c_int32, [ctypes.c_void_p]),
     "pv_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "pv_device_info": (ctypes.c_int32, [ctypes.c_void_p, _P(ctypes.c_int32), _P(ctypes.c_int64)]),
+    "pv_set_l2_fetch_bytes": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, _P(ctypes.c_int32)]),
     "pv_register_column": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int32,
                                             ctypes.c_void_p, ctypes.c_int64, _P(ctypes.c_int32)]),
     "pv_column_stats": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, _P(ctypes.c_int64), _P(ctypes.c_int64)]),
@@ -432,6 +433,13 @@ class Context:
         sm, l2 = ctypes.c_int32(), ctypes.c_int64()
         self._check(self.lib.pv_device_info(self.h, ctypes.byref(sm), ctypes.byref(l2)))
         return sm.value, l2.value
+
+    def set_l2_fetch_bytes(self, nbytes: int) -> int:
+        """L2 fetch granularity of this process's CUDA context on the device
+        (pv_set_l2_fetch_bytes: 0, 32, 64 or 128); returns the previous value."""
+        prev = ctypes.c_int32()
+        self._check(self.lib.pv_set_l2_fetch_bytes(self.h, int(nbytes), ctypes.byref(prev)))
+        return prev.value
 
     def last_launch_count(self) -> int:
         n = ctypes.c_int32()

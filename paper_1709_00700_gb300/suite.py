@@ -534,8 +534,11 @@ def main(argv=None):
     ap.add_argument("--restat", action="store_true", help="with --timings-in: recompute the queries' statistics")
     ap.add_argument("--online", action="store_true", help="also run the run-time re-tuning experiment")
     ap.add_argument("--summary-out", default="", help="compact record of the figures (no per-query rows)")
+    ap.add_argument("--l2-fetch-bytes", type=int, default=32, choices=[0, 32, 64, 128],
+                    help="L2 fetch granularity of the CUDA context (pv_set_l2_fetch_bytes), as the benchmark sets it")
     a = ap.parse_args(argv)
     ctx = pv.Context(0)
+    ctx.set_l2_fetch_bytes(a.l2_fetch_bytes)
     if a.graphs:
         print(json.dumps(graph_experiment(ctx)))
         ctx.close()
@@ -590,7 +593,7 @@ def compact_record(summary: dict, args, argv=None) -> dict:
             "alg1_variants_run", "alg1_configs")
     rec = {"command": "python -m paper_1709_00700_gb300.suite " + " ".join(argv if argv is not None else sys.argv[1:]),
            "seed": 1709, "rows": [args.min_rows, args.max_rows], "reps": args.reps,
-           "kernel_source_hash": build.source_hash(),
+           "l2_fetch_bytes": getattr(args, "l2_fetch_bytes", None), "kernel_source_hash": build.source_hash(),
            "explored": {k: summary[k] for k in keep if k in summary}}
     if "confirmed" in summary:
         rec["confirmed"] = {k: v for k, v in summary["confirmed"].items() if k != "per_query"}

@@ -782,6 +782,41 @@ def test_compacted_two_first_stage_items(ctx, n):
     ctx.sync()
 
 
+def test_l2_fetch_granularity_keeps_results(ctx):
+    """pv_set_l2_fetch_bytes changes how much an L2 miss fetches, never what a
+    pipeline computes: a join, a compacted projection and the grouped
+    benchmark shape at each granularity, against the oracle; the previous
+    value comes back and other values are rejected."""
+    s = _star_small(100_003, seed=81)
+    register(ctx, s)
+    t = {"t": datagen.table_filter_agg(100_003, seed=82)}
+    register(ctx, t)
+    li = {"li": datagen.table_lowcard_groups(100_003, seed=83)}
+    register(ctx, li)
+    cases = [(workloads.star_plan(), s, pv.variant(agg="local", ht="perfect", pred="compacted", items_per_thread=2,
+                                                   block=512), True),
+             (workloads.filter_project_plan(), t, pv.variant(pred="compacted", exec="single", items_per_thread=1,
+                                                             first_items=2), False),
+             (workloads.lowcard_plan(), li, pv.variant(agg="local", ht="perfect", threads_per_table=1,
+                                                       pred="predicated", items_per_thread=1), True)]
+    wants = [want(plan, tabs) for plan, tabs, _, _ in cases]
+    first = ctx.set_l2_fetch_bytes(32)
+    try:
+        prev = 32
+        for nbytes in (64, 128, 0, 32):
+            assert ctx.set_l2_fetch_bytes(nbytes) == prev or prev == 0
+            prev = nbytes
+            for (plan, _, var, ordered), w in zip(cases, wants):
+                got = ctx.query(plan, var, pv.ht_variant("perfect"))
+                assert_same(got, w, ordered=ordered, ctxmsg=f"l2 fetch {nbytes}: {plan.get('fact')}")
+        for bad in (16, 256, -1):
+            with pytest.raises(pv.PVError) as e:
+                ctx.set_l2_fetch_bytes(bad)
+            assert e.value.status == -1
+    finally:
+        ctx.set_l2_fetch_bytes(first)
+
+
 def test_compacted_is_unsupported_where_it_does_not_apply(ctx):
     kv = {"kv": datagen.table_keyval(1000, 10, seed=3)}
     register(ctx, kv)
