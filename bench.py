@@ -494,7 +494,8 @@ def run_pv(args):
     rows = args.rows or w["rows"]
     tables, plan = make_tables(args.workload, rows, args.groups, args.dist)
     ctx = pv.Context(local)
-    ctx.set_l2_fetch_bytes(args.l2_fetch_bytes)
+    if args.l2_fetch_bytes:
+        ctx.set_l2_fetch_bytes(args.l2_fetch_bytes)
     dev = {t: {c: torch.from_numpy(np.ascontiguousarray(v)).cuda(local) for c, v in cols.items()}
            for t, cols in tables.items()}
     for t, cols in dev.items():
@@ -738,7 +739,8 @@ def run_pv_chain(args):
     rows = args.rows or w["rows"]
     tables, chain = datagen.tpch_schema(rows), workloads.q5_chain()
     ctx = pv.Context(local)
-    ctx.set_l2_fetch_bytes(args.l2_fetch_bytes)
+    if args.l2_fetch_bytes:
+        ctx.set_l2_fetch_bytes(args.l2_fetch_bytes)
     dev = {t: {c: torch.from_numpy(np.ascontiguousarray(v)).cuda(local) for c, v in cols.items()}
            for t, cols in tables.items()}
     for t, cols in dev.items():
@@ -917,7 +919,8 @@ def main():
                     help="no L2 flush between steps (hot-L2 numbers, labelled as such)")
     ap.add_argument("--cpu-threads", type=int, default=0, help="oracle threads (0 = all host cores)")
     ap.add_argument("--l2-fetch-bytes", type=int, default=32, choices=[0, 32, 64, 128],
-                    help="L2 fetch granularity of the CUDA context (pv_set_l2_fetch_bytes; 0 = driver's choice)")
+                    help="L2 fetch granularity of the CUDA context (pv_set_l2_fetch_bytes); 0 leaves the "
+                         "context's initial setting")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

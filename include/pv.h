@@ -221,13 +221,14 @@ const char* pv_last_error(const pv_ctx* ctx);
 /* Multiprocessor count and L2 bytes of the ctx device. */
 pv_status pv_device_info(pv_ctx* ctx, int32_t* sm_count, int64_t* l2_bytes);
 /* L2 fetch granularity of the process's CUDA context on the ctx device (the context limit
- * cudaLimitMaxL2FetchGranularity): the bytes an L2 miss fetches from DRAM at most, 0 (the driver's choice), 32,
- * 64 or 128.  Not in the paper: a memory-system setting for the lazily loaded columns of branched and
- * compacted execution (Section 6), whose rows are read sparsely; at 32 bytes DRAM moves closer to the
- * sector-exact bytes.  The limit belongs to the CUDA context, so it applies to every kernel the process launches
- * on that device afterwards (this library's and others'), and it ends with the process: no GPU setting
- * changes.  *previous (optional) receives the value in force before the call.  Other values are
- * PV_ERR_INVALID_ARG; the runtime refusing the limit is PV_ERR_CUDA.  Blocks; not capturable. */
+ * cudaLimitMaxL2FetchGranularity): the bytes an L2 miss fetches from DRAM at most, 32, 64 or 128.  Not in the
+ * paper: a memory-system setting for the lazily loaded columns of branched and compacted execution (Section
+ * 6), whose rows are read sparsely.  At 32 bytes DRAM moves the sector-exact bytes; a context never given a
+ * value fetched whole 128-byte lines for these kernels on GB300 (although the runtime reports 64 for it).
+ * The limit belongs to the CUDA context, so it applies to every kernel the process launches on that device
+ * afterwards (this library's and others'), and it ends with the process: no GPU setting changes.  *previous
+ * (optional) receives the value the runtime reports before the call.  Other values are PV_ERR_INVALID_ARG;
+ * the runtime refusing the limit is PV_ERR_CUDA.  Blocks; not capturable. */
 pv_status pv_set_l2_fetch_bytes(pv_ctx* ctx, int32_t bytes, int32_t* previous);
 
 /* Registers a borrowed device column (column-major table storage, Section

@@ -845,8 +845,8 @@ pv_status pv_device_info(pv_ctx* c, int32_t* sm_count, int64_t* l2_bytes) {
 
 pv_status pv_set_l2_fetch_bytes(pv_ctx* c, int32_t bytes, int32_t* previous) {
   if (!c) return PV_ERR_INVALID_ARG;
-  if (bytes != 0 && bytes != 32 && bytes != 64 && bytes != 128)
-    return fail(c, PV_ERR_INVALID_ARG, "L2 fetch bytes must be 0, 32, 64 or 128");
+  if (bytes != 32 && bytes != 64 && bytes != 128)
+    return fail(c, PV_ERR_INVALID_ARG, "L2 fetch bytes must be 32, 64 or 128");
   if (c->capturing) return fail(c, PV_ERR_INVALID_ARG, "pv_set_l2_fetch_bytes cannot be captured");
   PV_CUDA(c, cudaSetDevice(c->device));
   size_t old = 0;

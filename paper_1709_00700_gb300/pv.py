@@ -436,7 +436,7 @@ class Context:
 
     def set_l2_fetch_bytes(self, nbytes: int) -> int:
         """L2 fetch granularity of this process's CUDA context on the device
-        (pv_set_l2_fetch_bytes: 0, 32, 64 or 128); returns the previous value."""
+        (pv_set_l2_fetch_bytes: 32, 64 or 128); returns the previous value."""
         prev = ctypes.c_int32()
         self._check(self.lib.pv_set_l2_fetch_bytes(self.h, int(nbytes), ctypes.byref(prev)))
         return prev.value

@@ -535,10 +535,12 @@ def main(argv=None):
     ap.add_argument("--online", action="store_true", help="also run the run-time re-tuning experiment")
     ap.add_argument("--summary-out", default="", help="compact record of the figures (no per-query rows)")
     ap.add_argument("--l2-fetch-bytes", type=int, default=32, choices=[0, 32, 64, 128],
-                    help="L2 fetch granularity of the CUDA context (pv_set_l2_fetch_bytes), as the benchmark sets it")
+                    help="L2 fetch granularity of the CUDA context (pv_set_l2_fetch_bytes), as the benchmark sets it; 0 "
+                         "leaves the context's initial setting")
     a = ap.parse_args(argv)
     ctx = pv.Context(0)
-    ctx.set_l2_fetch_bytes(a.l2_fetch_bytes)
+    if a.l2_fetch_bytes:
+        ctx.set_l2_fetch_bytes(a.l2_fetch_bytes)
     if a.graphs:
         print(json.dumps(graph_experiment(ctx)))
         ctx.close()

@@ -803,18 +803,18 @@ def test_l2_fetch_granularity_keeps_results(ctx):
     first = ctx.set_l2_fetch_bytes(32)
     try:
         prev = 32
-        for nbytes in (64, 128, 0, 32):
-            assert ctx.set_l2_fetch_bytes(nbytes) == prev or prev == 0
+        for nbytes in (64, 128, 32):
+            assert ctx.set_l2_fetch_bytes(nbytes) == prev
             prev = nbytes
             for (plan, _, var, ordered), w in zip(cases, wants):
                 got = ctx.query(plan, var, pv.ht_variant("perfect"))
                 assert_same(got, w, ordered=ordered, ctxmsg=f"l2 fetch {nbytes}: {plan.get('fact')}")
-        for bad in (16, 256, -1):
+        for bad in (0, 16, 256, -1):
             with pytest.raises(pv.PVError) as e:
                 ctx.set_l2_fetch_bytes(bad)
             assert e.value.status == -1
     finally:
-        ctx.set_l2_fetch_bytes(first)
+        ctx.set_l2_fetch_bytes(first if first in (32, 64, 128) else 64)
 
 
 def test_compacted_is_unsupported_where_it_does_not_apply(ctx):
